@@ -1,0 +1,155 @@
+/*
+ * dso.h -- C ABI of the GB300 diabatic split-operator library.
+ *
+ * Propagates an S-component nuclear wavepacket psi_s(q) on a periodic
+ * D-dimensional Fourier grid under the separable diabatic Hamiltonian
+ * H = p^T m^{-1} p / 2 * 1 + V(q)  (Eq. (diab_mol_ham), Sec. II H of
+ * Roulet, Choi, Vanicek, arXiv:1903.04946), with the second-order VTV
+ * split-operator step (Eq. (so_VTV)) and its recursive symmetric triple-jump
+ * and Suzuki-fractal compositions (Sec. II D-E) of orders 2..10, using the
+ * pruned splitting coefficients and unique-coefficient index arrays of
+ * Sec. II F (Eq. (merging_splitting_coeff_b_zero), Eq. (range_index_unq)).
+ * The kinetic and potential actions are applied in the momentum and position
+ * representations, switched by the library's own FFT kernels (Sec. II G).
+ *
+ * Conventions (all entry points):
+ *  - atomic units, hbar = 1;
+ *  - grid axis d has n[d] points q_k = qmin[d] + k (qmax[d]-qmin[d])/n[d],
+ *    k = 0..n[d]-1 (periodic, right endpoint excluded);
+ *  - psi is complex128 (interleaved re, im), surface-major
+ *    [S][n_0][n_1]...[n_{D-1}], last axis contiguous;
+ *  - the potential is real symmetric, passed packed as the upper triangle
+ *    [S(S+1)/2][n_0]...[n_{D-1}] float64, pairs (r,c), r <= c, row-major:
+ *    (0,0),(0,1),(1,1) for S = 2; (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) for S = 3;
+ *  - `where` arguments say where a caller buffer lives: DSO_HOST (pageable or
+ *    pinned host memory) or DSO_DEVICE (device memory of the context's GPU).
+ *
+ * Ownership: the caller owns every buffer it passes; the library copies in
+ * and out and keeps no caller pointer after a call returns.  The library
+ * owns the context, its device wavefunction, operator tables and work
+ * buffers, all released by dso_destroy.
+ *
+ * Errors: every call returns a dso_status and never aborts.  On failure the
+ * context is unchanged (except for the error text) unless stated otherwise;
+ * dso_last_error gives a message for the calling thread.
+ *
+ * Threads and streams: a context is used by one thread at a time.  All GPU
+ * work of a context is issued on its stream; calls that return results to
+ * host memory synchronise that stream.
+ */
+#ifndef DSO_H
+#define DSO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dso_ctx dso_ctx;
+
+typedef enum {
+  DSO_OK = 0,
+  DSO_EINVAL = -1,   /* bad argument or unsupported configuration */
+  DSO_ENOMEM = -2,   /* device allocation failed */
+  DSO_ECUDA = -3,    /* CUDA runtime error */
+  DSO_ESTATE = -4,   /* call out of order (e.g. propagate before set_psi) */
+  DSO_ETIMEOUT = -5, /* reserved: a bounded device wait gave up */
+  DSO_ENUMERIC = -6  /* non-finite input or result */
+} dso_status;
+
+enum { DSO_HOST = 0, DSO_DEVICE = 1 };
+enum { DSO_FP64 = 0, DSO_FP32 = 1 };
+enum { DSO_TRIPLE_JUMP = 0, DSO_SUZUKI = 1 };
+enum { DSO_VTV = 0, DSO_TVT = 1 };
+
+/* Limits of this build. */
+#define DSO_MAX_DIM 3
+#define DSO_MAX_SURFACES 4
+#define DSO_MIN_AXIS 8
+#define DSO_MAX_AXIS 4096
+
+/* Create a context on CUDA device `device`.  precision must be DSO_FP64
+ * (FP32 storage is not part of this build: DSO_EINVAL).  `cuda_stream` is a
+ * cudaStream_t owned by the caller, or NULL to let the context create and
+ * own a non-blocking stream.  *out receives the context (NULL on failure). */
+dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_stream);
+
+/* Release the context and every device buffer it owns.  NULL is a no-op. */
+void dso_destroy(dso_ctx* ctx);
+
+/* Grid of Sec. II G / App. B: D in 1..DSO_MAX_DIM axes, n[d] a power of two
+ * in [DSO_MIN_AXIS, DSO_MAX_AXIS], qmax[d] > qmin[d] (host arrays of length
+ * D).  Resets any loaded potential, masses, state and tables. */
+dso_status dso_set_grid(dso_ctx* ctx, int D, const int64_t* n, const double* qmin,
+                        const double* qmax);
+
+/* Diagonal mass matrix m of Eq. (diab_mol_ham): D positive values (host). */
+dso_status dso_set_masses(dso_ctx* ctx, const double* m);
+
+/* Diabatic potential V(q) of Eq. (diab_mol_ham): S in 2..DSO_MAX_SURFACES
+ * surfaces, packed upper triangle as described above, finite values.
+ * Copied to the device; resets the state and the tables. */
+dso_status dso_load_potential(dso_ctx* ctx, int S, const double* V, int where);
+
+/* Composition of Sec. II D-F: order in {2,4,6,8,10}; scheme DSO_TRIPLE_JUMP
+ * or DSO_SUZUKI; elementary must be DSO_VTV (Eq. (so_VTV): V acts first and
+ * last; DSO_TVT is not part of this build); prune must be 1 (the
+ * coefficients of Eq. (merging_splitting_coeff_b_zero)). */
+dso_status dso_set_scheme(dso_ctx* ctx, int order, int scheme, int elementary, int prune);
+
+/* Set psi (complex128, [S][grid]) from host or device memory. */
+dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);
+
+/* Advance psi by time t with step dt (dt may be negative; t/dt must be a
+ * non-negative integer within 1e-9 relative, else DSO_EINVAL).  Each step
+ * applies U_V(a~_1 dt) U_T(b~_1 dt) ... U_T(b~_{N_B} dt) U_V(a~_{N_B+1} dt)
+ * in the order of the general split-operator product of Sec. II E.
+ * Asynchronous on the context's stream. */
+dso_status dso_propagate(dso_ctx* ctx, double t, double dt);
+
+/* Copy psi (complex128, [S][grid]) to host or device memory.  A host copy
+ * synchronises the stream. */
+dso_status dso_get_psi(dso_ctx* ctx, void* out, int where);
+
+/* Observables of Sec. II A on the current psi, in FP64: norm = ||psi||,
+ * energy = <psi|H|psi> (kinetic part in the momentum representation,
+ * potential part in the position representation), pops[s] = ||psi_s||^2
+ * (host array of S entries).  Any output pointer may be NULL.  Synchronises
+ * the stream. */
+dso_status dso_observables(dso_ctx* ctx, double* norm, double* energy, double* pops);
+
+/* Pruned splitting coefficients of a composed scheme (Sec. II D-F), host
+ * only (no context, no GPU): a~ has n_a = N_B + 1 entries and b~ n_b = N_B
+ * (the substeps per time step); ia/ib are 0-based indices into the lists of
+ * unique values (Eq. (range_index_unq)), whose lengths go to n_a_unq and
+ * n_b_unq (Table II).  Output arrays may be NULL to query sizes; non-NULL
+ * arrays must hold n_a (a, ia), n_b (b, ib) entries. */
+dso_status dso_scheme_coefficients(int order, int scheme, int* n_a, int* n_b, double* a, double* b,
+                                   int* ia, int* ib, int* n_a_unq, int* n_b_unq);
+
+/* Diagnostics: advance psi by `nsteps` time steps of the current scheme
+ * (the pass list of the steps after the first) with plain launches and a
+ * CUDA event pair around every kernel on the context's stream, then report
+ * per kind of pass: axis, flags (bit 0 inverse FFT first, bit 1 forward FFT,
+ * bit 2 kinetic phase + inverse FFT, bit 8 one potential unitary, bit 9 a
+ * second one), surfaces staged per tile, launches per time step and the
+ * average duration of one launch in milliseconds.  At most max_kinds kinds
+ * are written; *n_kinds receives the number of kinds.  Synchronises. */
+dso_status dso_profile_steps(dso_ctx* ctx, double dt, int nsteps, int max_kinds, int* n_kinds, int* axis,
+                             int* flags, int* surfaces, int* launches_per_step, double* avg_ms);
+
+/* Number of kernel launches this context has issued since creation
+ * (diagnostics: counts each launch of the library's own kernels, including
+ * those inside CUDA-graph replays). */
+int64_t dso_launch_count(const dso_ctx* ctx);
+
+/* Message for the last failed call on this thread (never NULL; valid until
+ * the next call on this thread). */
+const char* dso_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSO_H */

@@ -1,0 +1,241 @@
+"""Python binding of the GB300 diabatic split-operator library (include/dso.h).
+
+Argument marshalling only: every function here forwards to the C entry point
+of the same name in ``libdso_gb300.so``; all propagation work runs in the
+library's CUDA kernels.  Host arrays are numpy (or CPU torch) arrays, device
+arrays are CUDA torch tensors; streams are torch CUDA streams (or raw
+cudaStream_t integers).  There is no CPU fallback: if the library is missing
+or cannot be loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build  # noqa: F401
+
+DSO_OK, DSO_EINVAL, DSO_ENOMEM, DSO_ECUDA, DSO_ESTATE, DSO_ETIMEOUT, DSO_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
+DSO_HOST, DSO_DEVICE = 0, 1
+DSO_FP64, DSO_FP32 = 0, 1
+DSO_TRIPLE_JUMP, DSO_SUZUKI = 0, 1
+DSO_VTV, DSO_TVT = 0, 1
+
+EXPORTS = (
+    "dso_create", "dso_destroy", "dso_set_grid", "dso_set_masses", "dso_load_potential",
+    "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
+    "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
+)
+
+_lib = None
+
+
+class DSOError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.dso_last_error().decode() if _lib is not None else "library not loaded"
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB):
+    """Load the shared library (it must have been built with ``build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run paper_1903_04946_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    pd, pi = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "dso_create": (i32, [ctypes.POINTER(vp), i32, i32, vp]),
+        "dso_destroy": (None, [vp]),
+        "dso_set_grid": (i32, [vp, i32, ctypes.POINTER(i64), pd, pd]),
+        "dso_set_masses": (i32, [vp, pd]),
+        "dso_load_potential": (i32, [vp, i32, vp, i32]),
+        "dso_set_scheme": (i32, [vp, i32, i32, i32, i32]),
+        "dso_set_psi": (i32, [vp, vp, i32]),
+        "dso_propagate": (i32, [vp, dbl, dbl]),
+        "dso_get_psi": (i32, [vp, vp, i32]),
+        "dso_observables": (i32, [vp, pd, pd, pd]),
+        "dso_scheme_coefficients": (i32, [i32, i32, pi, pi, pd, pd, pi, pi, pi, pi]),
+        "dso_profile_steps": (i32, [vp, dbl, i32, i32, pi, pi, pi, pi, pi, pd]),
+        "dso_launch_count": (i64, [vp]),
+        "dso_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != DSO_OK:
+        raise DSOError(status, where)
+
+
+def _ptr(buf, writable=False):
+    """(pointer, where) of a numpy array or torch tensor (C-contiguous)."""
+    try:
+        import torch
+        if isinstance(buf, torch.Tensor):
+            if not buf.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return ctypes.c_void_p(buf.data_ptr()), (DSO_DEVICE if buf.is_cuda else DSO_HOST)
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.asarray(buf)
+    if not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    if writable and not arr.flags["WRITEABLE"]:
+        raise ValueError("array must be writeable")
+    return ctypes.c_void_p(arr.ctypes.data), DSO_HOST
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# --- entry points, same names as include/dso.h -----------------------------
+
+def dso_create(device: int = 0, precision: int = DSO_FP64, stream=None):
+    lib = load()
+    ctx = ctypes.c_void_p()
+    _check(lib.dso_create(ctypes.byref(ctx), device, precision, _stream_handle(stream)), "dso_create")
+    return ctx
+
+
+def dso_destroy(ctx):
+    load().dso_destroy(ctx)
+
+
+def dso_set_grid(ctx, n, qmin, qmax):
+    D = len(n)
+    _check(load().dso_set_grid(ctx, D, (ctypes.c_int64 * D)(*[int(x) for x in n]),
+                               (ctypes.c_double * D)(*[float(x) for x in qmin]),
+                               (ctypes.c_double * D)(*[float(x) for x in qmax])), "dso_set_grid")
+
+
+def dso_set_masses(ctx, m):
+    D = len(m)
+    _check(load().dso_set_masses(ctx, (ctypes.c_double * D)(*[float(x) for x in m])), "dso_set_masses")
+
+
+def dso_load_potential(ctx, S, V):
+    if isinstance(V, np.ndarray):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+    p, where = _ptr(V)
+    _check(load().dso_load_potential(ctx, int(S), p, where), "dso_load_potential")
+
+
+def dso_set_scheme(ctx, order, scheme=DSO_TRIPLE_JUMP, elementary=DSO_VTV, prune=1):
+    _check(load().dso_set_scheme(ctx, order, scheme, elementary, prune), "dso_set_scheme")
+
+
+def dso_set_psi(ctx, psi):
+    if isinstance(psi, np.ndarray):
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    p, where = _ptr(psi)
+    _check(load().dso_set_psi(ctx, p, where), "dso_set_psi")
+
+
+def dso_propagate(ctx, t, dt):
+    _check(load().dso_propagate(ctx, float(t), float(dt)), "dso_propagate")
+
+
+def dso_get_psi(ctx, out):
+    p, where = _ptr(out, writable=True)
+    _check(load().dso_get_psi(ctx, p, where), "dso_get_psi")
+    return out
+
+
+def dso_observables(ctx, S):
+    norm, energy = ctypes.c_double(), ctypes.c_double()
+    pops = (ctypes.c_double * S)()
+    _check(load().dso_observables(ctx, ctypes.byref(norm), ctypes.byref(energy), pops), "dso_observables")
+    return norm.value, energy.value, np.array(pops[:], dtype=np.float64)
+
+
+def dso_scheme_coefficients(order, scheme=DSO_TRIPLE_JUMP):
+    """(a~, b~, I^a, I^b, N_a^unq, N_b^unq) of a composed scheme (host only)."""
+    lib = load()
+    na, nb, nau, nbu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.dso_scheme_coefficients(order, scheme, ctypes.byref(na), ctypes.byref(nb), None, None, None, None,
+                                       ctypes.byref(nau), ctypes.byref(nbu)), "dso_scheme_coefficients")
+    a = (ctypes.c_double * na.value)()
+    b = (ctypes.c_double * nb.value)()
+    ia = (ctypes.c_int * na.value)()
+    ib = (ctypes.c_int * nb.value)()
+    _check(lib.dso_scheme_coefficients(order, scheme, None, None, a, b, ia, ib, None, None),
+           "dso_scheme_coefficients")
+    return (np.array(a[:]), np.array(b[:]), np.array(ia[:]), np.array(ib[:]), nau.value, nbu.value)
+
+
+def dso_profile_steps(ctx, dt, nsteps, max_kinds=16):
+    """Per kind of pass: dicts with axis, flags, surfaces, launches_per_step,
+    avg_ms (CUDA events around every launch on the context's stream)."""
+    lib = load()
+    nk = ctypes.c_int()
+    ax, fl, sv, cnt = [(ctypes.c_int * max_kinds)() for _ in range(4)]
+    ms = (ctypes.c_double * max_kinds)()
+    _check(lib.dso_profile_steps(ctx, float(dt), int(nsteps), max_kinds, ctypes.byref(nk), ax, fl, sv, cnt, ms),
+           "dso_profile_steps")
+    return [dict(axis=ax[k], flags=fl[k], surfaces=sv[k], launches_per_step=cnt[k], avg_ms=ms[k])
+            for k in range(min(nk.value, max_kinds))]
+
+
+def dso_launch_count(ctx) -> int:
+    return int(load().dso_launch_count(ctx))
+
+
+def dso_last_error() -> str:
+    return load().dso_last_error().decode()
+
+
+class Context:
+    """Owns one dso context; a convenience holder over the functions above."""
+
+    def __init__(self, problem=None, device: int = 0, stream=None, order: int = 2,
+                 scheme: int = DSO_TRIPLE_JUMP):
+        self.ctx = dso_create(device, DSO_FP64, stream)
+        self.S = None
+        self.shape = None
+        if problem is not None:
+            self.load_problem(problem)
+            dso_set_scheme(self.ctx, order, scheme)
+
+    def load_problem(self, pr):
+        dso_set_grid(self.ctx, pr.n, pr.qmin, pr.qmax)
+        dso_set_masses(self.ctx, pr.mass)
+        dso_load_potential(self.ctx, pr.S, pr.V)
+        dso_set_psi(self.ctx, pr.psi0)
+        self.S = pr.S
+        self.shape = (pr.S,) + tuple(pr.n)
+
+    def propagate(self, t, dt):
+        dso_propagate(self.ctx, t, dt)
+
+    def psi(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.complex128)
+        return dso_get_psi(self.ctx, out)
+
+    def observables(self):
+        return dso_observables(self.ctx, self.S)
+
+    def close(self):
+        if self.ctx is not None:
+            dso_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,326 @@
+// axis_pass.cuh -- fused FFT / potential / kinetic pass along one grid axis.
+//
+// One CTA owns a tile of whole lines along axis `a` (length L) of the grid:
+// G neighbouring line positions, and for a potential pass all SV = S surfaces
+// of those positions.  The tile is staged in shared memory; each FFT stage
+// moves 8 complex values per thread into registers, applies the twiddles and
+// a radix-8 (or radix-4/2 for the leftover factor) butterfly, and writes the
+// results back in Stockham autosort order, so every transform ends in natural
+// order without a bit-reversal pass.
+//
+// Per pass, in this order (each step optional, chosen by `flags`):
+//   1. inverse FFT along the axis                              (Sec. II G)
+//   2. psi(q) <- U_V(a dt) psi(q): S x S complex matvec at every grid point
+//      with a precomputed unitary, then optionally a second one (the last V
+//      of a time step merged into the first V of the next)     (Sec. II H)
+//   3. forward FFT along the axis
+//   4. psi~(p) <- tau_b(p) psi~(p) with the kinetic phase (the 1/P of the
+//      inverse transforms folded in), then the inverse FFT      (Sec. II G)
+// Steps 2 need the wavepacket in the position representation on all axes,
+// step 4 in the momentum representation on all axes; the host orders the
+// passes so that this holds.
+//
+// The FP64 path on this GPU is bound by the FP64 pipe (one DFMA per SM
+// sub-partition every 64 cycles for a full warp), so the butterflies are
+// written to minimise FP64 instructions: trivial twiddles (+-1, +-i) cost
+// nothing, the (1 -+ i)/sqrt(2) factors of the radix-8 butterfly fold into
+// FMAs, and everything else (indexing, shared-memory traffic, table loads)
+// runs on other pipes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pass_args.h"
+
+namespace dso {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+// multiply by -i (forward) or +i (inverse): free, no FP64 instruction
+template <bool INV>
+__device__ __forceinline__ double2 rot_i(double2 a) {
+  return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
+
+// In-place DFT of length 2, 4, 8 with sign -1 (forward) or +1 (INV).
+template <bool INV>
+__device__ __forceinline__ void dft2(double2& a, double2& b) {
+  double2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(double2& a0, double2& a1, double2& a2, double2& a3) {
+  double2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  double2 t2 = cadd(a1, a3), t3 = rot_i<INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// 8-point DFT by one radix-2 split into two 4-point DFTs:
+// y_k = E_k + w^k O_k, y_{k+4} = E_k - w^k O_k, w = exp(-+2 pi i / 8).
+template <bool INV>
+__device__ __forceinline__ void dft8(double2* x) {
+  const double c = 0.70710678118654752440;  // 1/sqrt(2)
+  double2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  double2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  // k = 0
+  x[0] = cadd(e0, o0);
+  x[4] = csub(e0, o0);
+  // k = 2: w^2 = -+i
+  double2 r2 = rot_i<INV>(o2);
+  x[2] = cadd(e2, r2);
+  x[6] = csub(e2, r2);
+  // k = 1: w = (1 -+ i)/sqrt(2); w*o = c * u
+  double2 u1 = INV ? make_double2(o1.x - o1.y, o1.x + o1.y) : make_double2(o1.x + o1.y, o1.y - o1.x);
+  x[1] = make_double2(fma(c, u1.x, e1.x), fma(c, u1.y, e1.y));
+  x[5] = make_double2(fma(-c, u1.x, e1.x), fma(-c, u1.y, e1.y));
+  // k = 3: w^3 = (-1 -+ i)/sqrt(2)
+  double2 u3 = INV ? make_double2(-(o3.x + o3.y), o3.x - o3.y) : make_double2(o3.y - o3.x, -(o3.x + o3.y));
+  x[3] = make_double2(fma(c, u3.x, e3.x), fma(c, u3.y, e3.y));
+  x[7] = make_double2(fma(-c, u3.x, e3.x), fma(-c, u3.y, e3.y));
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftR(double2* x) {
+  if constexpr (R == 8) {
+    dft8<INV>(x);
+  } else if constexpr (R == 4) {
+    dft4<INV>(x[0], x[1], x[2], x[3]);
+  } else {
+    dft2<INV>(x[0], x[1]);
+  }
+}
+
+// Radix plan of a length-L transform: as many radix-8 stages as possible,
+// the leftover factor (2 or 4) as the first stage, whose twiddles are all 1.
+template <int L>
+struct Plan {
+  static constexpr int log2L = (L >= 4096) ? 12 : (L >= 2048) ? 11 : (L >= 1024) ? 10 : (L >= 512) ? 9
+                             : (L >= 256) ? 8 : (L >= 128) ? 7 : (L >= 64) ? 6 : (L >= 32) ? 5 : (L >= 16) ? 4 : 3;
+  static constexpr int rem = log2L % 3;           // 0, 1 or 2 leftover binary stages
+  static constexpr int first = rem == 0 ? 8 : (rem == 1 ? 2 : 4);
+  static constexpr int n8 = log2L / 3 - (rem == 0 ? 1 : 0);  // radix-8 stages after the first
+};
+
+// One Stockham stage of radix R on every line of the tile held in `sm`.
+// Thread-slot s of this thread owns 8 consecutive butterfly inputs' worth of
+// work: 8/R butterflies j = u*(8/R) + beta of line `line`.
+template <int L, int R, bool INV, int K>
+__device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double2* __restrict__ tw,
+                                               int nslots, int tid, int nthr) {
+  constexpr int NB = 8 / R;      // butterflies per slot
+  constexpr int Q = L / R;       // butterflies per line
+  double2 v[K][8];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int gid = s * nthr + tid;
+    if (gid < nslots) {
+      const int line = gid / (L / 8);
+      const int u = gid % (L / 8);
+      const double2* ln = sm + (size_t)line * L;
+#pragma unroll
+      for (int beta = 0; beta < NB; ++beta) {
+        const int j = u * NB + beta;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[s][beta * R + r] = ln[j + r * Q];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int gid = s * nthr + tid;
+    if (gid < nslots) {
+      const int line = gid / (L / 8);
+      const int u = gid % (L / 8);
+      double2* ln = sm + (size_t)line * L;
+#pragma unroll
+      for (int beta = 0; beta < NB; ++beta) {
+        const int j = u * NB + beta;
+        const int k = j & (Ls - 1);
+        double2* x = &v[s][beta * R];
+        if (Ls > 1) {
+          const int step = (L / (Ls * R)) * k;
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            const double2 w = __ldg(&tw[r * step]);
+            x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
+          }
+        }
+        dftR<R, INV>(x);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) ln[base + r * Ls] = x[r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, bool INV, int K>
+__device__ __forceinline__ void fft_lines(double2* sm, const double2* __restrict__ tw, int nslots, int tid, int nthr) {
+  using PL = Plan<L>;
+  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr);
+  int Ls = PL::first;
+#pragma unroll 1
+  for (int st = 0; st < PL::n8; ++st) {
+    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr);
+    Ls *= 8;
+  }
+}
+
+// Global address (within one surface) of element n of tile line g.
+struct TileGeom {
+  long long o0;      // first outer index of the tile
+  long long i0;      // first inner index of the tile
+  int Wi;            // inner positions per outer row in the tile
+  __device__ __forceinline__ long long addr(int g, int n, long long L, long long stride) const {
+    const long long o = o0 + g / Wi;
+    const long long i = i0 + g % Wi;
+    return o * L * stride + (long long)n * stride + i;
+  }
+};
+
+// Element e of the tile in address order -> (g, n); consecutive e are
+// consecutive addresses whenever the axis stride allows it.
+__device__ __forceinline__ void tile_elem(int e, int L, int Wi, int& g, int& n) {
+  const int i = e % Wi;
+  n = (e / Wi) % L;
+  const int o = e / (Wi * L);
+  g = o * Wi + i;
+}
+
+template <int SV>
+__device__ __forceinline__ void apply_potential(double2* sm, const double2* __restrict__ U, const TileGeom& tg,
+                                                int L, int G, long long stride, long long P, int tid, int nthr) {
+  constexpr int NP = SV * (SV + 1) / 2;
+  const int tile_pts = G * L;
+  for (int e = tid; e < tile_pts; e += nthr) {
+    int g, n;
+    tile_elem(e, L, tg.Wi, g, n);
+    const long long gi = tg.addr(g, n, L, stride);
+    const int off = g * L + n;
+    double2 x[SV], y[SV];
+#pragma unroll
+    for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + off];
+    double2 u[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) u[k] = __ldg(&U[(size_t)k * P + gi]);
+#pragma unroll
+    for (int r = 0; r < SV; ++r) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < SV; ++c) {
+        const int lo = r < c ? r : c, hi = r < c ? c : r;
+        const int k = lo * SV - lo * (lo - 1) / 2 + (hi - lo);
+        if (c == 0) {
+          acc = cmul(u[k], x[c]);
+        } else {
+          acc.x = fma(u[k].x, x[c].x, acc.x);
+          acc.x = fma(-u[k].y, x[c].y, acc.x);
+          acc.y = fma(u[k].x, x[c].y, acc.y);
+          acc.y = fma(u[k].y, x[c].x, acc.y);
+        }
+      }
+      y[r] = acc;
+    }
+#pragma unroll
+    for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + off] = y[s];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void apply_kinetic(double2* sm, const double2* __restrict__ tau, const TileGeom& tg,
+                                              int L, int G, int SVl, long long stride, int tid, int nthr) {
+  const int tile_pts = G * L;
+  for (int e = tid; e < tile_pts; e += nthr) {
+    int g, n;
+    tile_elem(e, L, tg.Wi, g, n);
+    const double2 t = __ldg(&tau[tg.addr(g, n, L, stride)]);
+    const int off = g * L + n;
+    for (int s = 0; s < SVl; ++s) {
+      double2* p = &sm[(size_t)s * tile_pts + off];
+      *p = cmul(*p, t);
+    }
+  }
+  __syncthreads();
+}
+
+// SV: surfaces staged together (S for passes with a potential step, 1 else).
+// Each thread owns one 8-element work slot per FFT stage, so a CTA has
+// SV * G * L / 8 threads; MaxThreads<L, SV> bounds it.
+template <int L, int SV>
+struct MaxThreads {
+  static constexpr int value = (SV * L / 8 > 256) ? SV * L / 8 : 256;
+};
+
+template <int L, int SV>
+__global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(PassArgs a) {
+  constexpr int K = 1;
+  extern __shared__ double2 sm[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int G = a.G;
+  const int tile_pts = G * L;
+  const long long tiles_per_surface = a.lines / G;
+  long long tile = blockIdx.x;
+  int surf0 = 0;
+  if (SV == 1) {
+    surf0 = (int)(tile / tiles_per_surface);
+    tile = tile % tiles_per_surface;
+  }
+  // line id lambda = o * stride + i; the tile covers lambdas [tile*G, tile*G+G)
+  TileGeom tg;
+  const long long lam0 = tile * G;
+  tg.Wi = (int)(a.stride < G ? a.stride : G);
+  tg.o0 = lam0 / a.stride;
+  tg.i0 = lam0 % a.stride;
+
+  // load
+  for (int s = 0; s < SV; ++s) {
+    const double2* src = a.psi + (size_t)(surf0 + s) * a.P;
+    for (int e = tid; e < tile_pts; e += nthr) {
+      int g, n;
+      tile_elem(e, L, tg.Wi, g, n);
+      sm[(size_t)s * tile_pts + g * L + n] = src[tg.addr(g, n, L, a.stride)];
+    }
+  }
+  __syncthreads();
+
+  const int nslots = SV * G * (L / 8);
+  if (a.flags & PASS_INV_FIRST) fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr);
+  if (SV > 1) {  // the host sets U1/U2 only for passes that stage all S surfaces
+    if (a.U1) apply_potential<SV>(sm, a.U1, tg, L, G, a.stride, a.P, tid, nthr);
+    if (a.U2) apply_potential<SV>(sm, a.U2, tg, L, G, a.stride, a.P, tid, nthr);
+  }
+  if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, a.tw, nslots, tid, nthr);
+  if (a.flags & PASS_T) {
+    apply_kinetic(sm, a.tau, tg, L, G, SV, a.stride, tid, nthr);
+    fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr);
+  }
+
+  // store
+  for (int s = 0; s < SV; ++s) {
+    double2* dst = a.psi + (size_t)(surf0 + s) * a.P;
+    for (int e = tid; e < tile_pts; e += nthr) {
+      int g, n;
+      tile_elem(e, L, tg.Wi, g, n);
+      dst[tg.addr(g, n, L, a.stride)] = sm[(size_t)s * tile_pts + g * L + n];
+    }
+  }
+}
+
+}  // namespace dso

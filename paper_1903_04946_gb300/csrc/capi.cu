@@ -1,0 +1,666 @@
+// capi.cu -- the C ABI of include/dso.h: context, validation, pass planning,
+// operator tables, CUDA-graph replay of a composed time step.
+//
+// A time step of the pruned composition (Sec. II E-F) is
+//   U_V(a~_1 dt) U_T(b~_1 dt) U_V(a~_2 dt) ... U_T(b~_NB dt) U_V(a~_{NB+1} dt)
+// acting right to left in the paper's product, i.e. V(a~_1) first.  Each
+// kinetic action needs the momentum representation (Sec. II G): a forward
+// FFT over every axis, the phase, an inverse FFT over every axis.  The passes
+// (kernels over whole lines of one axis, see axis_pass.cuh) are ordered so
+// that FFTs along axis 0 are fused with the potential step and FFTs along the
+// last axis with the kinetic step:
+//   D = 1:  [V(a~_j) F0 T(b~_j) I0] per substep, final [V(a~_{NB+1})];
+//   D >= 2: [I0 V(a~_j) F0] [F1] .. [F_{D-1} T(b~_j) I_{D-1}] .. [I1] per
+//           substep; the last potential action of a step and the first of the
+//           next run in the same pass; final [I0 V(a~_{NB+1})].
+// All steps after the first have the same pass list, which is captured once
+// into a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dso.h"
+#include "dso_internal.h"
+
+using namespace dso;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+dso_status fail(dso_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+struct Pass {
+  int axis;
+  int SV;
+  int flags;
+  int u1, u2;  // unique-a table indices or -1
+  int tb;      // unique-b table index or -1
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct dso_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // grid
+  int D = 0;
+  int64_t n[DSO_MAX_DIM] = {1, 1, 1};
+  double qmin[DSO_MAX_DIM] = {0, 0, 0}, qmax[DSO_MAX_DIM] = {0, 0, 0};
+  double mass[DSO_MAX_DIM] = {0, 0, 0};
+  bool have_grid = false, have_mass = false;
+  long long P = 0;
+  // model and state
+  int S = 0;
+  double* V = nullptr;       // packed [S(S+1)/2][P]
+  double2* psi = nullptr;    // [S][P]
+  bool have_V = false, have_psi = false;
+  // scheme
+  int order = 2, scheme = DSO_TRIPLE_JUMP;
+  Coeffs coeffs;
+  bool have_coeffs = false;
+  // tables for one dt
+  bool tables_valid = false;
+  double tables_dt = 0.0;
+  double2* Utab = nullptr;   // [na][S(S+1)/2][P]
+  double2* tau = nullptr;    // [nb][P]
+  double* tau_a = nullptr;   // [na] a_unq * dt
+  double2* tw[13] = {};      // per log2 L
+  // observables
+  double* Tax = nullptr;     // per-axis p^2 / (2 m_d), concatenated
+  double2* work = nullptr;   // [S][P]
+  double* partials = nullptr;
+  double* obs_out = nullptr;
+  // graph of one middle time step
+  cudaGraphExec_t step_exec = nullptr;
+  int step_exec_passes = 0;
+  // tile lines per (axis) chosen for this grid
+  int G[DSO_MAX_DIM][2] = {};
+  int64_t launches = 0;
+};
+
+namespace {
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((1LL << l) < v) ++l;
+  return l;
+}
+
+void drop_graph(dso_ctx* c) {
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  c->step_exec = nullptr;
+  c->step_exec_passes = 0;
+}
+
+void drop_tables(dso_ctx* c) {
+  drop_graph(c);
+  dfree(c->Utab);
+  dfree(c->tau);
+  dfree(c->tau_a);
+  c->tables_valid = false;
+}
+
+void drop_model(dso_ctx* c) {
+  drop_tables(c);
+  dfree(c->V);
+  dfree(c->psi);
+  dfree(c->Tax);
+  dfree(c->work);
+  dfree(c->partials);
+  dfree(c->obs_out);
+  c->have_V = c->have_psi = false;
+}
+
+// Tile lines per surface for a pass along `axis` staging SV surfaces: the
+// largest power of two giving at most about 128 threads (8 values each) per
+// CTA, so that many CTAs share each SM and the last wave is short.  A power
+// of two always divides the line count and either divides the axis stride or
+// is a multiple of it, which the tile geometry relies on.
+int choose_G(const dso_ctx* c, int axis, int SV) {
+  const int L = (int)c->n[axis];
+  const long long lines = c->P / L;
+  const long long target = (128LL * 8) / ((long long)SV * L);
+  const long long gmax = axis_pass_max_tile_lines(L, SV);
+  long long G = 1;
+  while (G * 2 <= target && G * 2 <= gmax && G * 2 <= lines) G *= 2;
+  return (int)G;
+}
+
+cudaError_t run_pass(dso_ctx* c, const Pass& p) {
+  const int L = (int)c->n[p.axis];
+  PassArgs a;
+  a.psi = c->psi;
+  const int NP = c->S * (c->S + 1) / 2;
+  a.U1 = p.u1 >= 0 ? c->Utab + (size_t)p.u1 * NP * c->P : nullptr;
+  a.U2 = p.u2 >= 0 ? c->Utab + (size_t)p.u2 * NP * c->P : nullptr;
+  a.tau = p.tb >= 0 ? c->tau + (size_t)p.tb * c->P : nullptr;
+  a.tw = c->tw[ilog2(L)];
+  a.P = c->P;
+  long long stride = 1;
+  for (int d = p.axis + 1; d < c->D; ++d) stride *= c->n[d];
+  a.stride = stride;
+  a.lines = c->P / L;
+  a.S = c->S;
+  a.G = c->G[p.axis][p.SV == 1 ? 0 : 1];
+  a.flags = p.flags;
+  if (a.G < 1 || (a.G & (a.G - 1)) || a.lines % a.G) return cudaErrorInvalidConfiguration;
+  const long long ntiles = (p.SV == c->S) ? a.lines / a.G : (long long)c->S * a.lines / a.G;
+  c->launches += 1;
+  return launch_axis_pass(L, p.SV, a, ntiles, c->stream);
+}
+
+// Pass list of time step `s_first` (true: the first step of a propagate call).
+std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
+  std::vector<Pass> out;
+  const int NB = (int)c->coeffs.b.size();
+  const int last = (int)c->coeffs.a.size() - 1;
+  const int D = c->D;
+  for (int j = 0; j < NB; ++j) {
+    int u1 = c->coeffs.ia[j], u2 = -1;
+    if (j == 0 && !first) {
+      u1 = c->coeffs.ia[last];
+      u2 = c->coeffs.ia[0];
+    }
+    const int tb = c->coeffs.ib[j];
+    if (D == 1) {
+      out.push_back(Pass{0, c->S, PASS_FWD | PASS_T, u1, u2, tb});
+      continue;
+    }
+    const int inv_first = (j == 0 && first) ? 0 : PASS_INV_FIRST;
+    out.push_back(Pass{0, c->S, inv_first | PASS_FWD, u1, u2, -1});
+    for (int d = 1; d <= D - 2; ++d) out.push_back(Pass{d, 1, PASS_FWD, -1, -1, -1});
+    out.push_back(Pass{D - 1, 1, PASS_FWD | PASS_T, -1, -1, tb});
+    for (int d = D - 2; d >= 1; --d) out.push_back(Pass{d, 1, PASS_INV_FIRST, -1, -1, -1});
+  }
+  return out;
+}
+
+Pass final_pass(const dso_ctx* c) {
+  const int last = (int)c->coeffs.a.size() - 1;
+  return Pass{0, c->S, c->D == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last], -1, -1};
+}
+
+#define CK(expr)                                                                                  \
+  do {                                                                                            \
+    cudaError_t _e = (expr);                                                                      \
+    if (_e != cudaSuccess)                                                                        \
+      return fail(_e == cudaErrorMemoryAllocation ? DSO_ENOMEM : DSO_ECUDA,                       \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                            \
+  } while (0)
+
+dso_status ensure_twiddles(dso_ctx* c) {
+  for (int d = 0; d < c->D; ++d) {
+    const int l = ilog2(c->n[d]);
+    if (c->tw[l]) continue;
+    std::vector<double2> h = host_twiddles((int)c->n[d]);
+    CK(cudaMalloc(&c->tw[l], h.size() * sizeof(double2)));
+    CK(cudaMemcpy(c->tw[l], h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  }
+  return DSO_OK;
+}
+
+dso_status ensure_tables(dso_ctx* c, double dt) {
+  if (c->tables_valid && c->tables_dt == dt) return DSO_OK;
+  drop_tables(c);
+  dso_status st = ensure_twiddles(c);
+  if (st != DSO_OK) return st;
+  const int na = (int)c->coeffs.a_unq.size(), nb = (int)c->coeffs.b_unq.size();
+  const int NP = c->S * (c->S + 1) / 2;
+  CK(cudaMalloc(&c->Utab, (size_t)na * NP * c->P * sizeof(double2)));
+  CK(cudaMalloc(&c->tau, (size_t)nb * c->P * sizeof(double2)));
+  CK(cudaMalloc(&c->tau_a, (size_t)na * sizeof(double)));
+  std::vector<double> ta(na);
+  for (int u = 0; u < na; ++u) ta[u] = c->coeffs.a_unq[u] * dt;
+  CK(cudaMemcpyAsync(c->tau_a, ta.data(), na * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(launch_potential_tables(c->Utab, c->V, c->tau_a, na, c->S, c->P, c->stream));
+  c->launches += 1;
+  std::vector<double2> fac = host_kinetic_factors(c->D, c->n, c->qmin, c->qmax, c->mass, c->coeffs.b_unq, dt);
+  double2* dfac = nullptr;
+  CK(cudaMalloc(&dfac, fac.size() * sizeof(double2)));
+  cudaError_t e = cudaMemcpyAsync(dfac, fac.data(), fac.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = launch_kinetic_tables(c->tau, dfac, nb, c->D, c->n, c->P, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dfac);
+  CK(e);
+  c->launches += 1;
+  c->tables_valid = true;
+  c->tables_dt = dt;
+  return DSO_OK;
+}
+
+dso_status ensure_step_graph(dso_ctx* c) {
+  if (c->step_exec) return DSO_OK;
+  std::vector<Pass> passes = step_passes(c, false);
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  const int64_t before = c->launches;
+  for (const Pass& p : passes) {
+    err = run_pass(c, p);
+    if (err != cudaSuccess) break;
+  }
+  c->launches = before;  // captured, not launched
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+  if (err == cudaSuccess) err = e2;
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&c->step_exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  CK(err);
+  c->step_exec_passes = (int)passes.size();
+  return DSO_OK;
+}
+
+dso_status check_ready(dso_ctx* c) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (!c->have_grid) return fail(DSO_ESTATE, "grid not set");
+  if (!c->have_V) return fail(DSO_ESTATE, "potential not loaded");
+  if (!c->have_mass) return fail(DSO_ESTATE, "masses not set");
+  if (!c->have_psi) return fail(DSO_ESTATE, "wavefunction not set");
+  return DSO_OK;
+}
+
+dso_status ensure_coeffs(dso_ctx* c) {
+  if (c->have_coeffs) return DSO_OK;
+  c->coeffs = build_coefficients(c->order, c->scheme);
+  c->have_coeffs = true;
+  return DSO_OK;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_stream) {
+  if (!out) return fail(DSO_EINVAL, "out is null");
+  *out = nullptr;
+  if (precision != DSO_FP64) return fail(DSO_EINVAL, "only DSO_FP64 is part of this build");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(DSO_ECUDA, "no CUDA device");
+  if (device < 0 || device >= ndev) return fail(DSO_EINVAL, "device index out of range");
+  DeviceGuard g(device);
+  if (!g.ok) return fail(DSO_ECUDA, "cudaSetDevice failed");
+  dso_ctx* c = new (std::nothrow) dso_ctx();
+  if (!c) return fail(DSO_ENOMEM, "host allocation failed");
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return fail(DSO_ECUDA, "stream creation failed");
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return DSO_OK;
+}
+
+void dso_destroy(dso_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_model(c);
+  for (auto& t : c->tw) dfree(t);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+dso_status dso_set_grid(dso_ctx* c, int D, const int64_t* n, const double* qmin, const double* qmax) {
+  if (!c || !n || !qmin || !qmax) return fail(DSO_EINVAL, "null argument");
+  if (D < 1 || D > DSO_MAX_DIM) return fail(DSO_EINVAL, "D must be 1..3");
+  for (int d = 0; d < D; ++d) {
+    if (!is_pow2(n[d]) || n[d] < DSO_MIN_AXIS || n[d] > DSO_MAX_AXIS)
+      return fail(DSO_EINVAL, "each n[d] must be a power of two in [8, 4096]");
+    if (!std::isfinite(qmin[d]) || !std::isfinite(qmax[d]) || !(qmax[d] > qmin[d]))
+      return fail(DSO_EINVAL, "need finite qmin < qmax on every axis");
+  }
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_model(c);
+  c->D = D;
+  c->P = 1;
+  for (int d = 0; d < DSO_MAX_DIM; ++d) {
+    c->n[d] = d < D ? n[d] : 1;
+    c->qmin[d] = d < D ? qmin[d] : 0.0;
+    c->qmax[d] = d < D ? qmax[d] : 0.0;
+    c->P *= c->n[d];
+  }
+  c->have_grid = true;
+  c->have_mass = false;
+  return DSO_OK;
+}
+
+dso_status dso_set_masses(dso_ctx* c, const double* m) {
+  if (!c || !m) return fail(DSO_EINVAL, "null argument");
+  if (!c->have_grid) return fail(DSO_ESTATE, "grid not set");
+  for (int d = 0; d < c->D; ++d)
+    if (!std::isfinite(m[d]) || !(m[d] > 0)) return fail(DSO_EINVAL, "masses must be finite and positive");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_tables(c);
+  dfree(c->Tax);
+  for (int d = 0; d < c->D; ++d) c->mass[d] = m[d];
+  c->have_mass = true;
+  return DSO_OK;
+}
+
+dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
+  if (!c || !V) return fail(DSO_EINVAL, "null argument");
+  if (!c->have_grid) return fail(DSO_ESTATE, "grid not set");
+  if (S < 2 || S > DSO_MAX_SURFACES) return fail(DSO_EINVAL, "S must be 2..4");
+  if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
+  for (int d = 0; d < c->D; ++d)
+    if (!axis_pass_supported((int)c->n[d], d == 0 ? S : 1) || (c->D == 1 && !axis_pass_supported((int)c->n[0], S)))
+      return fail(DSO_EINVAL, "axis length too long for this surface count (S * n[0] must be <= 8192)");
+  const size_t count = (size_t)(S * (S + 1) / 2) * c->P;
+  if (where == DSO_HOST) {
+    for (size_t i = 0; i < count; ++i)
+      if (!std::isfinite(V[i])) return fail(DSO_ENUMERIC, "potential has a non-finite value");
+  }
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_model(c);
+  c->S = S;
+  CK(cudaMalloc(&c->V, count * sizeof(double)));
+  CK(cudaMemcpyAsync(c->V, V, count * sizeof(double), where == DSO_HOST ? cudaMemcpyHostToDevice
+                                                                         : cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMalloc(&c->psi, (size_t)S * c->P * sizeof(double2)));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int d = 0; d < c->D; ++d) {
+    c->G[d][0] = choose_G(c, d, 1);
+    c->G[d][1] = choose_G(c, d, S);
+  }
+  c->have_V = true;
+  return DSO_OK;
+}
+
+dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int prune) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (order < 2 || order > 10 || order % 2) return fail(DSO_EINVAL, "order must be 2, 4, 6, 8 or 10");
+  if (scheme != DSO_TRIPLE_JUMP && scheme != DSO_SUZUKI) return fail(DSO_EINVAL, "unknown scheme");
+  if (elementary != DSO_VTV) return fail(DSO_EINVAL, "only the VTV elementary method is part of this build");
+  if (prune != 1) return fail(DSO_EINVAL, "only pruned coefficients are part of this build");
+  try {
+    Coeffs cf = build_coefficients(order, scheme);
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    drop_tables(c);
+    c->coeffs = cf;
+    c->order = order;
+    c->scheme = scheme;
+    c->have_coeffs = true;
+  } catch (const std::exception& ex) {
+    return fail(DSO_EINVAL, ex.what());
+  }
+  return DSO_OK;
+}
+
+dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {
+  if (!c || !psi) return fail(DSO_EINVAL, "null argument");
+  if (!c->have_V) return fail(DSO_ESTATE, "load the potential first (it fixes S)");
+  if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
+  const size_t bytes = (size_t)c->S * c->P * sizeof(double2);
+  if (where == DSO_HOST) {
+    const double* p = (const double*)psi;
+    for (size_t i = 0; i < 2 * (size_t)c->S * c->P; ++i)
+      if (!std::isfinite(p[i])) return fail(DSO_ENUMERIC, "psi has a non-finite value");
+  }
+  DeviceGuard g(c->device);
+  CK(cudaMemcpyAsync(c->psi, psi, bytes, where == DSO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                     c->stream));
+  if (where == DSO_HOST) CK(cudaStreamSynchronize(c->stream));
+  c->have_psi = true;
+  return DSO_OK;
+}
+
+dso_status dso_propagate(dso_ctx* c, double t, double dt) {
+  dso_status st = check_ready(c);
+  if (st != DSO_OK) return st;
+  if (!std::isfinite(t) || !std::isfinite(dt) || dt == 0.0) return fail(DSO_EINVAL, "t and dt must be finite, dt != 0");
+  const double ratio = t / dt;
+  const double nr = std::round(ratio);
+  if (nr < 0 || std::fabs(ratio - nr) > 1e-9 * std::fmax(1.0, std::fabs(ratio)))
+    return fail(DSO_EINVAL, "t / dt must be a non-negative integer");
+  const long long nsteps = (long long)nr;
+  if (nsteps == 0) return DSO_OK;
+  DeviceGuard g(c->device);
+  try {
+    st = ensure_coeffs(c);
+    if (st != DSO_OK) return st;
+    st = ensure_tables(c, dt);
+    if (st != DSO_OK) return st;
+    for (const Pass& p : step_passes(c, true)) CK(run_pass(c, p));
+    if (nsteps > 1) {
+      const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
+      if (capturable) {
+        st = ensure_step_graph(c);
+        if (st != DSO_OK) return st;
+        for (long long s = 1; s < nsteps; ++s) {
+          CK(cudaGraphLaunch(c->step_exec, c->stream));
+          c->launches += c->step_exec_passes;
+        }
+      } else {
+        const std::vector<Pass> mid = step_passes(c, false);
+        for (long long s = 1; s < nsteps; ++s)
+          for (const Pass& p : mid) CK(run_pass(c, p));
+      }
+    }
+    CK(run_pass(c, final_pass(c)));
+  } catch (const std::exception& ex) {
+    return fail(DSO_EINVAL, ex.what());
+  }
+  return DSO_OK;
+}
+
+dso_status dso_get_psi(dso_ctx* c, void* out, int where) {
+  if (!c || !out) return fail(DSO_EINVAL, "null argument");
+  if (!c->have_psi) return fail(DSO_ESTATE, "wavefunction not set");
+  if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
+  DeviceGuard g(c->device);
+  const size_t bytes = (size_t)c->S * c->P * sizeof(double2);
+  CK(cudaMemcpyAsync(out, c->psi, bytes, where == DSO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     c->stream));
+  if (where == DSO_HOST) CK(cudaStreamSynchronize(c->stream));
+  return DSO_OK;
+}
+
+dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pops) {
+  dso_status st = check_ready(c);
+  if (st != DSO_OK) return st;
+  DeviceGuard g(c->device);
+  st = ensure_twiddles(c);
+  if (st != DSO_OK) return st;
+  if (!c->Tax) {
+    std::vector<double> h;
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int d = 0; d < c->D; ++d)
+      for (int64_t k = 0; k < c->n[d]; ++k) {
+        const int64_t kk = (k < c->n[d] / 2) ? k : k - c->n[d];
+        const long double p = two_pi * (long double)kk / ((long double)c->qmax[d] - (long double)c->qmin[d]);
+        h.push_back((double)(p * p / (2.0L * (long double)c->mass[d])));
+      }
+    CK(cudaMalloc(&c->Tax, h.size() * sizeof(double)));
+    CK(cudaMemcpy(c->Tax, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * sizeof(double2)));
+  if (!c->partials) CK(cudaMalloc(&c->partials, (size_t)obs_partial_blocks() * DSO_OBS_COLS * sizeof(double)));
+  if (!c->obs_out) CK(cudaMalloc(&c->obs_out, DSO_OBS_COLS * sizeof(double)));
+  // momentum representation of a copy: forward FFT along every axis
+  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  double2* keep = c->psi;
+  c->psi = c->work;
+  cudaError_t e = cudaSuccess;
+  for (int d = 0; d < c->D && e == cudaSuccess; ++d) e = run_pass(c, Pass{d, 1, PASS_FWD, -1, -1, -1});
+  c->psi = keep;
+  CK(e);
+  ObsArgs a;
+  a.psi = c->psi;
+  a.psik = c->work;
+  a.V = c->V;
+  a.Tax = c->Tax;
+  for (int d = 0; d < 3; ++d) a.n[d] = c->n[d];
+  a.D = c->D;
+  a.S = c->S;
+  a.P = c->P;
+  CK(launch_observables(a, c->partials, c->obs_out, c->stream));
+  c->launches += 2;
+  double h[DSO_OBS_COLS];
+  CK(cudaMemcpyAsync(h, c->obs_out, (c->S + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double dV = 1.0;
+  for (int d = 0; d < c->D; ++d) dV *= (c->qmax[d] - c->qmin[d]) / (double)c->n[d];
+  double tot = 0.0;
+  for (int s = 0; s < c->S; ++s) {
+    if (pops) pops[s] = h[s] * dV;
+    tot += h[s];
+  }
+  if (norm) *norm = std::sqrt(tot * dV);
+  if (energy) *energy = h[c->S] * dV + h[c->S + 1] * dV / (double)c->P;
+  if (!std::isfinite(tot) || !std::isfinite(h[c->S]) || !std::isfinite(h[c->S + 1]))
+    return fail(DSO_ENUMERIC, "non-finite observable");
+  return DSO_OK;
+}
+
+dso_status dso_scheme_coefficients(int order, int scheme, int* n_a, int* n_b, double* a, double* b, int* ia,
+                                   int* ib, int* n_a_unq, int* n_b_unq) {
+  Coeffs cf;
+  try {
+    cf = build_coefficients(order, scheme);
+  } catch (const std::exception& ex) {
+    return fail(DSO_EINVAL, ex.what());
+  }
+  if (n_a) *n_a = (int)cf.a.size();
+  if (n_b) *n_b = (int)cf.b.size();
+  if (n_a_unq) *n_a_unq = (int)cf.a_unq.size();
+  if (n_b_unq) *n_b_unq = (int)cf.b_unq.size();
+  if (a) std::memcpy(a, cf.a.data(), cf.a.size() * sizeof(double));
+  if (b) std::memcpy(b, cf.b.data(), cf.b.size() * sizeof(double));
+  if (ia) std::memcpy(ia, cf.ia.data(), cf.ia.size() * sizeof(int));
+  if (ib) std::memcpy(ib, cf.ib.data(), cf.ib.size() * sizeof(int));
+  return DSO_OK;
+}
+
+dso_status dso_profile_steps(dso_ctx* c, double dt, int nsteps, int max_kinds, int* n_kinds, int* axis, int* flags,
+                             int* surfaces, int* launches_per_step, double* avg_ms) {
+  dso_status st = check_ready(c);
+  if (st != DSO_OK) return st;
+  if (!std::isfinite(dt) || dt == 0.0 || nsteps < 1) return fail(DSO_EINVAL, "need finite dt != 0 and nsteps >= 1");
+  DeviceGuard g(c->device);
+  try {
+    st = ensure_coeffs(c);
+    if (st != DSO_OK) return st;
+    st = ensure_tables(c, dt);
+    if (st != DSO_OK) return st;
+  } catch (const std::exception& ex) {
+    return fail(DSO_EINVAL, ex.what());
+  }
+  const std::vector<Pass> passes = step_passes(c, false);
+  struct Kind {
+    int axis, flags, sv, count;
+    double ms;
+  };
+  std::vector<Kind> kinds;
+  std::vector<int> kind_of(passes.size());
+  for (size_t i = 0; i < passes.size(); ++i) {
+    const Pass& p = passes[i];
+    const int f = p.flags | (p.u1 >= 0 ? 256 : 0) | (p.u2 >= 0 ? 512 : 0);
+    int k = -1;
+    for (size_t j = 0; j < kinds.size(); ++j)
+      if (kinds[j].axis == p.axis && kinds[j].flags == f && kinds[j].sv == p.SV) k = (int)j;
+    if (k < 0) {
+      kinds.push_back(Kind{p.axis, f, p.SV, 0, 0.0});
+      k = (int)kinds.size() - 1;
+    }
+    kinds[k].count += 1;
+    kind_of[i] = k;
+  }
+  std::vector<cudaEvent_t> ev(2 * passes.size(), nullptr);
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&x);
+  for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+    for (size_t i = 0; i < passes.size() && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(ev[2 * i], c->stream);
+      if (e == cudaSuccess) e = run_pass(c, passes[i]);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    for (size_t i = 0; i < passes.size() && e == cudaSuccess; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      kinds[kind_of[i]].ms += ms;
+    }
+  }
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  CK(e);
+  if (n_kinds) *n_kinds = (int)kinds.size();
+  for (int k = 0; k < (int)kinds.size() && k < max_kinds; ++k) {
+    if (axis) axis[k] = kinds[k].axis;
+    if (flags) flags[k] = kinds[k].flags;
+    if (surfaces) surfaces[k] = kinds[k].sv;
+    if (launches_per_step) launches_per_step[k] = kinds[k].count;
+    if (avg_ms) avg_ms[k] = kinds[k].ms / ((double)kinds[k].count * nsteps);
+  }
+  return DSO_OK;
+}
+
+int64_t dso_launch_count(const dso_ctx* c) { return c ? c->launches : 0; }
+
+const char* dso_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+namespace dso {
+
+bool axis_pass_supported(int L, int SV) {
+  if (L < 8 || L > 4096 || (L & (L - 1))) return false;
+  if (SV < 1 || SV > 4) return false;
+  return (long long)SV * L <= 8192;
+}
+
+int axis_pass_max_tile_lines(int L, int SV) {
+  const int maxt = (SV * L / 8 > 256) ? SV * L / 8 : 256;
+  int g = (maxt * 8) / (SV * L);
+  return g < 1 ? 1 : g;
+}
+
+cudaError_t launch_axis_pass(int L, int SV, const PassArgs& a, long long ntiles, cudaStream_t st) {
+  switch (SV) {
+    case 1: return launch_axis_pass_sv1(L, a, ntiles, st);
+    case 2: return launch_axis_pass_sv2(L, a, ntiles, st);
+    case 3: return launch_axis_pass_sv3(L, a, ntiles, st);
+    case 4: return launch_axis_pass_sv4(L, a, ntiles, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dso

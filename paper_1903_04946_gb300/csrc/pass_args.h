@@ -1,0 +1,28 @@
+// pass_args.h -- host-visible parameters of one axis pass (axis_pass.cuh).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dso {
+
+enum PassFlags : int {
+  PASS_INV_FIRST = 1,  // inverse FFT before the potential step
+  PASS_FWD = 2,        // forward FFT after the potential step
+  PASS_T = 4,          // kinetic phase then inverse FFT after the forward FFT
+};
+
+struct PassArgs {
+  double2* psi;            // [S][P] wavefunction (in/out)
+  const double2* U1;       // [S(S+1)/2][P] potential unitary, or null
+  const double2* U2;       // second potential unitary, or null
+  const double2* tau;      // [P] kinetic phase (1/P folded in), or null
+  const double2* tw;       // [L] exp(-2 pi i m / L), m = 0..L-1
+  long long P;             // grid points per surface
+  long long stride;        // element stride of the axis (product of later axes)
+  long long lines;         // lines per surface = P / L
+  int S;                   // surfaces
+  int G;                   // lines per surface in one tile (power of two)
+  int flags;
+};
+
+}  // namespace dso

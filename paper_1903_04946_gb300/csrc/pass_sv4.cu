@@ -1,0 +1,8 @@
+// pass_sv4.cu -- axis-pass kernels staging 4 surface(s) per tile.
+#include "pass_launch.cuh"
+
+namespace dso {
+cudaError_t launch_axis_pass_sv4(int L, const PassArgs& a, long long ntiles, cudaStream_t st) {
+  return launch_by_length<4>(L, a, ntiles, st);
+}
+}  // namespace dso

@@ -1,0 +1,97 @@
+"""CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports
+every entry point declared in include/dso.h, and its host-only coefficient
+code reproduces Table II and the oracle's coefficients.  No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1903_04946_gb300 as dso
+from oracle import coefficients as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    dso.build()
+    return dso.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(dso_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert declared, "no declarations found"
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(dso.EXPORTS) | (declared - set(dso.EXPORTS))
+    assert set(dso.EXPORTS) <= declared
+
+
+def test_library_targets_sm103a():
+    out = os.popen(f"/usr/local/cuda/bin/cuobjdump --list-elf {dso.LIB} 2>/dev/null").read()
+    if not out:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out
+
+
+def _table2():
+    rows = []
+    for line in open(os.path.join(ROOT, "tests", "golden", "table2.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        sch, o, before, after, na, nb = line.split()
+        rows.append((sch, int(o), int(after), int(na), int(nb)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _table2(), ids=lambda r: f"{r[0]}{r[1]}")
+def test_library_coefficients_match_table2(lib, row):
+    sch, order, after, na, nb = row
+    scheme = dso.DSO_SUZUKI if sch == "suzuki" else dso.DSO_TRIPLE_JUMP
+    a, b, ia, ib, nau, nbu = dso.dso_scheme_coefficients(order, scheme)
+    assert len(a) + len(b) == after
+    assert (nau, nbu) == (na, nb)
+    assert len(a) == len(b) + 1
+
+
+@pytest.mark.parametrize("scheme", [dso.DSO_TRIPLE_JUMP, dso.DSO_SUZUKI])
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10])
+def test_library_coefficients_match_oracle(lib, scheme, order):
+    a, b, ia, ib, nau, nbu = dso.dso_scheme_coefficients(order, scheme)
+    sp = C.Splitting(order, C.SUZUKI if scheme == dso.DSO_SUZUKI else C.TRIPLE_JUMP)
+    assert np.max(np.abs(a - np.array(sp.a))) <= 2e-16 * np.max(np.abs(a))
+    assert np.max(np.abs(b - np.array(sp.b))) <= 2e-16 * np.max(np.abs(b))
+    assert list(ia) == list(sp.Ia) and list(ib) == list(sp.Ib)
+
+
+def test_library_rejects_bad_scheme(lib):
+    with pytest.raises(dso.DSOError):
+        dso.dso_scheme_coefficients(3, dso.DSO_TRIPLE_JUMP)
+    with pytest.raises(dso.DSOError):
+        dso.dso_scheme_coefficients(4, 7)
+    assert "scheme" in dso.dso_last_error() or "order" in dso.dso_last_error()
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    ctx = ctypes.c_void_p()
+    st = lib.dso_create(ctypes.byref(ctx), 0, dso.DSO_FP64, None)
+    assert st != dso.DSO_OK
+    assert not ctx.value
