@@ -81,7 +81,7 @@ def test_time_reversible_on_gpu(dso):
     pr = synth.pyrazine_like(seed=9, n=(32, 32, 32))
     ctx = dso.Context(pr, order=6, scheme=dso.DSO_SUZUKI)
     ctx.propagate(200.0, 20.0)
-    ctx.propagate(200.0, -20.0)
+    ctx.propagate(-200.0, -20.0)
     back = ctx.psi()
     ctx.close()
     assert rel_l2(back, pr.psi0) < 1e-12
