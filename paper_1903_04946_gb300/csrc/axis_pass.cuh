@@ -116,12 +116,30 @@ struct Plan {
   static constexpr int n8 = log2L / 3 - (rem == 0 ? 1 : 0);  // radix-8 stages after the first
 };
 
+// Between FFT stages only the threads of one line exchange data.  A line of
+// length L is handled by L/8 consecutive threads, so for L <= 256 it lies in
+// one warp and a warp barrier suffices; longer lines span warps.
+// `wmask` holds the lanes of this thread's warp that exist in the block.
+template <int L>
+__device__ __forceinline__ void stage_sync(unsigned wmask) {
+  if constexpr (L <= 256) {
+    __syncwarp(wmask);
+  } else {
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ unsigned warp_lanes_mask(int tid, int nthr) {
+  const int left = nthr - (tid & ~31);
+  return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+}
+
 // One Stockham stage of radix R on every line of the tile held in `sm`.
 // Thread-slot s of this thread owns 8 consecutive butterfly inputs' worth of
 // work: 8/R butterflies j = u*(8/R) + beta of line `line`.
 template <int L, int R, bool INV, int K>
 __device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double2* __restrict__ tw,
-                                               int nslots, int tid, int nthr) {
+                                               int nslots, int tid, int nthr, unsigned wmask) {
   constexpr int NB = 8 / R;      // butterflies per slot
   constexpr int Q = L / R;       // butterflies per line
   double2 v[K][8];
@@ -140,7 +158,7 @@ __device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double
       }
     }
   }
-  __syncthreads();
+  stage_sync<L>(wmask);
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const int gid = s * nthr + tid;
@@ -168,17 +186,18 @@ __device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double
       }
     }
   }
-  __syncthreads();
+  stage_sync<L>(wmask);
 }
 
 template <int L, bool INV, int K>
 __device__ __forceinline__ void fft_lines(double2* sm, const double2* __restrict__ tw, int nslots, int tid, int nthr) {
   using PL = Plan<L>;
-  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr);
+  const unsigned wmask = warp_lanes_mask(tid, nthr);
+  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr, wmask);
   int Ls = PL::first;
 #pragma unroll 1
   for (int st = 0; st < PL::n8; ++st) {
-    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr);
+    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr, wmask);
     Ls *= 8;
   }
 }
@@ -301,16 +320,24 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   __syncthreads();
 
   const int nslots = SV * G * (L / 8);
-  if (a.flags & PASS_INV_FIRST) fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr);
+  // The tile-wide steps (load, potential, kinetic phase, store) walk the tile
+  // in address order and end with a block barrier; the FFT stages in between
+  // only synchronise the threads of each line.
+  if (a.flags & PASS_INV_FIRST) {
+    fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr);
+    __syncthreads();
+  }
   if (SV > 1) {  // the host sets U1/U2 only for passes that stage all S surfaces
     if (a.U1) apply_potential<SV>(sm, a.U1, tg, L, G, a.stride, a.P, tid, nthr);
     if (a.U2) apply_potential<SV>(sm, a.U2, tg, L, G, a.stride, a.P, tid, nthr);
   }
   if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, a.tw, nslots, tid, nthr);
   if (a.flags & PASS_T) {
+    __syncthreads();
     apply_kinetic(sm, a.tau, tg, L, G, SV, a.stride, tid, nthr);
     fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr);
   }
+  __syncthreads();
 
   // store
   for (int s = 0; s < SV; ++s) {

@@ -17,6 +17,7 @@
 // into a CUDA graph and replayed.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -102,6 +103,7 @@ struct dso_ctx {
   int step_exec_passes = 0;
   // tile lines per (axis) chosen for this grid
   int G[DSO_MAX_DIM][2] = {};
+  bool tuned = false;
   int64_t launches = 0;
 };
 
@@ -129,6 +131,7 @@ void drop_tables(dso_ctx* c) {
 
 void drop_model(dso_ctx* c) {
   drop_tables(c);
+  c->tuned = false;
   dfree(c->V);
   dfree(c->psi);
   dfree(c->Tax);
@@ -252,6 +255,77 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   c->launches += 1;
   c->tables_valid = true;
   c->tables_dt = dt;
+  return DSO_OK;
+}
+
+// Tile-size autotuner.  For every kind of pass the propagation uses, time
+// each admissible tile line count G (a power of two whose CTA is a whole
+// number of warps, when one exists) with CUDA events on a copy of psi and the
+// real operator tables, and keep the fastest.  The FFT work per amplitude
+// does not depend on G; G trades load balance across the SMs (many small
+// CTAs) against per-CTA overhead.  Skipped when DSO_AUTOTUNE=0.
+dso_status autotune_tiles(dso_ctx* c) {
+  if (c->tuned) return DSO_OK;
+  const char* env = getenv("DSO_AUTOTUNE");
+  if (env && env[0] == '0') {
+    c->tuned = true;
+    return DSO_OK;
+  }
+  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * sizeof(double2)));
+  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t err = cudaEventCreate(&e1);
+  double2* keep = c->psi;
+  c->psi = c->work;
+  const int64_t launches = c->launches;
+  for (int d = 0; d < c->D && err == cudaSuccess; ++d) {
+    const int svs[2] = {1, c->S};
+    for (int which = 0; which < 2 && err == cudaSuccess; ++which) {
+      const int SV = svs[which];
+      const bool vpass = (d == 0);
+      if ((SV == c->S) != vpass) continue;  // axis 0 stages all surfaces, the others one
+      Pass p{d, SV, PASS_FWD, -1, -1, -1};
+      if (vpass) {
+        p.u1 = 0;
+        p.flags = (c->D == 1) ? (PASS_FWD | PASS_T) : (PASS_INV_FIRST | PASS_FWD);
+        if (c->D == 1) p.tb = 0;
+      } else if (d == c->D - 1) {
+        p.flags = PASS_FWD | PASS_T;
+        p.tb = 0;
+      }
+      const int L = (int)c->n[d];
+      const long long lines = c->P / L;
+      const int gmax = axis_pass_max_tile_lines(L, SV);
+      bool any_whole = false;
+      for (long long G = 1; G <= gmax && G <= lines; G *= 2)
+        if ((SV * G * (L / 8)) % 32 == 0) any_whole = true;
+      float best = 1e30f;
+      int bestG = c->G[d][which];
+      for (long long G = 1; G <= gmax && G <= lines && err == cudaSuccess; G *= 2) {
+        if (any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
+        c->G[d][which] = (int)G;
+        err = run_pass(c, p);  // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_pass(c, p);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+          best = ms;
+          bestG = (int)G;
+        }
+      }
+      c->G[d][which] = bestG;
+    }
+  }
+  c->psi = keep;
+  c->launches = launches + (c->launches - launches);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  CK(err);
+  c->tuned = true;
   return DSO_OK;
 }
 
@@ -457,6 +531,11 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
     if (st != DSO_OK) return st;
     st = ensure_tables(c, dt);
     if (st != DSO_OK) return st;
+    if (!c->tuned) {
+      drop_graph(c);
+      st = autotune_tiles(c);
+      if (st != DSO_OK) return st;
+    }
     for (const Pass& p : step_passes(c, true)) CK(run_pass(c, p));
     if (nsteps > 1) {
       const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
@@ -579,6 +658,11 @@ dso_status dso_profile_steps(dso_ctx* c, double dt, int nsteps, int max_kinds, i
     if (st != DSO_OK) return st;
     st = ensure_tables(c, dt);
     if (st != DSO_OK) return st;
+    if (!c->tuned) {
+      drop_graph(c);
+      st = autotune_tiles(c);
+      if (st != DSO_OK) return st;
+    }
   } catch (const std::exception& ex) {
     return fail(DSO_EINVAL, ex.what());
   }

@@ -153,9 +153,9 @@ def test_errors_are_reported(dso):
         with pytest.raises(dso.DSOError) as ei:
             dso.dso_set_psi(ctx, bad)
         assert ei.value.status == dso.DSO_ENUMERIC
+        dso.dso_propagate(ctx, 0.0, 0.1)                   # zero steps: a no-op
+        dso.dso_set_grid(ctx, (4096,), (0.0,), (1.0,))
         with pytest.raises(dso.DSOError):
-            dso.dso_set_grid(ctx, (4096,), (0.0,), (1.0,))
             dso.dso_load_potential(ctx, 3, np.zeros((6, 4096)))  # S * n > 8192
-        dso.dso_propagate(ctx, 0.0, 0.1)
     finally:
         dso.dso_destroy(ctx)
