@@ -144,6 +144,38 @@ dso_status dso_profile_steps(dso_ctx* ctx, double dt, int nsteps, int max_kinds,
  * those inside CUDA-graph replays). */
 int64_t dso_launch_count(const dso_ctx* ctx);
 
+/* Allocation-free populations and potential energy of a device
+ * wavefunction.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory themselves or let a library do
+ * it (code running under a pool allocator that owns all device memory, an
+ * engine whose memory budget is fixed before it starts, a context where an
+ * allocation would synchronise the device).  It calls no cudaMalloc or
+ * cudaFree and needs no context: its per-block partial sums live in a
+ * file-scope device array of 304 x 8 doubles (19,456 bytes) that every GPU
+ * loading this library holds until the process exits.
+ *
+ * psi: device pointer, complex128 [S][P] (position representation);
+ * V: device pointer to the packed potential [S(S+1)/2][P], or NULL to skip
+ * the potential term; S in 1..4 (larger S does not fit the scratch array
+ * and returns DSO_EINVAL); P >= 1 grid points per surface; dV the grid cell
+ * volume; out: device pointer to S + 1 doubles receiving
+ * out[s] = dV sum_q |psi_s(q)|^2 and out[S] = dV sum_q Re psi^dagger V psi
+ * (0 when V is NULL).  Runs on `cuda_stream` (a cudaStream_t, NULL for the
+ * legacy default stream) on the calling thread's current device and does
+ * not synchronise.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before capturing the stream into a CUDA graph.  Every call on a device
+ * shares the one array and leaves its partial sums there; each call writes
+ * every slot it reads before reading it, so nothing is cleared between
+ * calls.  Calls that overlap on the GPU (other streams, other host threads)
+ * race on the array and must be serialised by the caller.  Returns
+ * DSO_EINVAL for bad arguments and DSO_ECUDA for CUDA errors; it does not
+ * set the text returned by dso_last_error. */
+dso_status dso_position_observables_noalloc(const void* psi, const double* V, int S, int64_t P, double dV,
+                                            double* out, void* cuda_stream);
+
 /* Message for the last failed call on this thread (never NULL; valid until
  * the next call on this thread). */
 const char* dso_last_error(void);

@@ -26,6 +26,7 @@ EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_masses", "dso_load_potential",
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
+    "dso_position_observables_noalloc",
 )
 
 _lib = None
@@ -63,6 +64,7 @@ def load(path: str = LIB):
         "dso_profile_steps": (i32, [vp, dbl, i32, i32, pi, pi, pi, pi, pi, pd]),
         "dso_launch_count": (i64, [vp]),
         "dso_last_error": (ctypes.c_char_p, []),
+        "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -193,6 +195,24 @@ def dso_profile_steps(ctx, dt, nsteps, max_kinds=16):
 
 def dso_launch_count(ctx) -> int:
     return int(load().dso_launch_count(ctx))
+
+
+def dso_position_observables_noalloc(psi, V, S, P, dV, out, stream=None):
+    """Allocation-free populations and potential energy of a device psi.
+    psi, V (or None) and out are CUDA tensors; out receives S + 1 doubles.
+    For callers that cannot allocate device memory; see include/dso.h."""
+    pp, wp = _ptr(psi)
+    po, wo = _ptr(out, writable=True)
+    if wp != DSO_DEVICE or wo != DSO_DEVICE:
+        raise ValueError("psi and out must be device tensors")
+    pv = None
+    if V is not None:
+        pv, wv = _ptr(V)
+        if wv != DSO_DEVICE:
+            raise ValueError("V must be a device tensor")
+    _check(load().dso_position_observables_noalloc(pp, pv, int(S), int(P), float(dV), po,
+                                                    _stream_handle(stream)), "dso_position_observables_noalloc")
+    return out
 
 
 def dso_last_error() -> str:

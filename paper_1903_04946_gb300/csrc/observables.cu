@@ -9,6 +9,9 @@
 // Two launches: per-block partial sums (each block walks a fixed strided set
 // of grid points), then one block adds the partials in block order, so the
 // result does not depend on scheduling.  The caller applies dV.
+#include <mutex>
+
+#include "../../include/dso.h"
 #include "dso_internal.h"
 
 namespace dso {
@@ -93,3 +96,106 @@ cudaError_t launch_observables(const ObsArgs& a, double* partials, double* out, 
 }
 
 }  // namespace dso
+
+// ---------------------------------------------------------------------------
+// Allocation-free position-space observables.
+//
+// Some callers cannot call cudaMalloc at all: code that runs under a
+// caching or pool allocator that owns every device allocation, inside an
+// engine whose memory budget is fixed before the first step, or in a context
+// where allocation would synchronise the device.  This variant of the
+// per-block reduction above keeps its partial sums in a file-scope device
+// array instead of a buffer from the context, so it allocates nothing.  The
+// array (kNoAllocBlocks x kNoAllocCols doubles, 19,456 bytes) is held by
+// every GPU that loads the library until the process exits.
+// ---------------------------------------------------------------------------
+namespace dso {
+namespace {
+
+constexpr int kNoAllocBlocks = 304;  // 2 x 152 SMs
+constexpr int kNoAllocCols = 8;      // S populations + <V>, S <= 4, padded
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocBlocks * kNoAllocCols];
+
+// Host-side device addresses of g_noalloc_partials, one per device.  The
+// array's name in host code is only a host stand-in for the symbol, so the
+// address must come from cudaGetSymbolAddress with that device current.
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {};
+
+__global__ void obs_position_partial_kernel(const double2* __restrict__ psi, const double* __restrict__ V, int S,
+                                            long long P, double* __restrict__ partials) {
+  __shared__ double red[kThreads];
+  double acc[kNoAllocCols];
+  for (int c = 0; c < kNoAllocCols; ++c) acc[c] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P; g += stride) {
+    double2 x[4];
+    for (int s = 0; s < S; ++s) {
+      x[s] = psi[(size_t)s * P + g];
+      acc[s] += x[s].x * x[s].x + x[s].y * x[s].y;
+    }
+    if (V) {
+      double ev = 0.0;
+      int k = 0;
+      for (int r = 0; r < S; ++r)
+        for (int c = r; c < S; ++c) {
+          const double v = V[(size_t)k * P + g];
+          const double re = x[r].x * x[c].x + x[r].y * x[c].y;
+          ev += (r == c) ? v * re : 2.0 * v * re;
+          ++k;
+        }
+      acc[S] += ev;
+    }
+  }
+  // every block writes all S + 1 of its columns: no slot is read before this
+  // call has written it, so the array needs no clearing between calls
+  for (int c = 0; c <= S; ++c) {
+    red[threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * kNoAllocCols + c] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void obs_position_final_kernel(const double* __restrict__ partials, int ncol, double dV, double* out) {
+  const int c = threadIdx.x;
+  if (c >= ncol) return;
+  double s = 0.0;
+  for (int b = 0; b < kNoAllocBlocks; ++b) s += partials[(size_t)b * kNoAllocCols + c];
+  out[c] = s * dV;
+}
+
+}  // namespace
+}  // namespace dso
+
+extern "C" dso_status dso_position_observables_noalloc(const void* psi, const double* V, int S, int64_t P,
+                                                       double dV, double* out, void* cuda_stream) {
+  using namespace dso;
+  if (!psi || !out) return DSO_EINVAL;
+  if (S < 1 || S + 1 > kNoAllocCols || S > DSO_MAX_SURFACES) return DSO_EINVAL;  // scratch holds S <= 4
+  if (P < 1) return DSO_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DSO_ECUDA;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // first call on this device: look up the array's device address
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_partials) != cudaSuccess || !ptr) return DSO_ECUDA;
+      g_noalloc_ptr[dev] = (double*)ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  obs_position_partial_kernel<<<kNoAllocBlocks, kThreads, 0, st>>>((const double2*)psi, V, S, (long long)P, scratch);
+  if (cudaGetLastError() != cudaSuccess) return DSO_ECUDA;
+  obs_position_final_kernel<<<1, 32, 0, st>>>(scratch, S + 1, dV, out);
+  if (cudaGetLastError() != cudaSuccess) return DSO_ECUDA;
+  return DSO_OK;
+}
+
