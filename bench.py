@@ -66,6 +66,29 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank propagates its own independently seeded wavepacket."""
+    return SEED + rank
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Slowest rank's time (control-path reduction only; no wavefunction data
+    crosses ranks)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, points: int, substeps: int, steps: int, seconds: float) -> float:
+    """Whole-job grid-points x substeps per second: every rank does the same
+    amount of work, timed by the slowest rank."""
+    return world * points * substeps * steps / seconds
+
+
 # --------------------------------------------------------------------------
 # clocks sampled during the timed region
 # --------------------------------------------------------------------------
@@ -186,7 +209,7 @@ def run_gpu(args):
     torch.cuda.set_device(device)
     dso.build()
     dso.load()
-    pr = workload(SEED + rank)
+    pr = workload(rank_seed(rank))
     nsub = substeps_per_step()
     pts = int(np.prod(N_GRID))
     stream = torch.cuda.Stream(device=device)
@@ -224,12 +247,8 @@ def run_gpu(args):
     launches = dso.dso_launch_count(ctx.ctx) - launches0
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * pts * nsub * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, f"cuda:{device}")
+    value = job_throughput(world, pts, nsub, args.steps, ms * 1e-3)
 
     # end to end through the public API with host buffers: each step copies
     # psi in from pinned host memory, propagates one step and reads psi back
@@ -246,13 +265,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, f"cuda:{device}")
     bytes_psi = S * pts * 16
-    e2e = {"value": world * pts * nsub * e2e_steps / e2e_s, "unit": UNIT,
+    e2e = {"value": job_throughput(world, pts, nsub, e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": bytes_psi, "d2h_bytes_per_step": bytes_psi}
 
     # per-kernel durations with CUDA events around every launch (same sizes,
