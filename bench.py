@@ -187,7 +187,8 @@ def kind_name(k):
         parts.append(f"F{k['axis']}")
     if f & 4:
         parts.append(f"T I{k['axis']}")
-    return "axis_pass_kernel<L=%d,SV=%d> [%s]" % (N_GRID[k["axis"]], k["surfaces"], " ".join(parts))
+    name = "axis_pass_pq_kernel" if k.get("variant") == 1 else "axis_pass_kernel"
+    return "%s<L=%d,SV=%d> [%s]" % (name, N_GRID[k["axis"]], k["surfaces"], " ".join(parts))
 
 
 # --------------------------------------------------------------------------
@@ -287,7 +288,8 @@ def run_gpu(args):
                 "peak_source": "FP64 unit count x max SM clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
                 "hbm_gbs_achieved": round(dom["bytes"] / (dom["avg_ms"] * 1e-3) / 1e9, 1),
                 "kinds": [{"kernel": kind_name(k), "avg_us": round(k["avg_ms"] * 1e3, 2),
-                           "launches_per_step": k["launches_per_step"],
+                           "launches_per_step": k["launches_per_step"], "tile_lines": k["tile_lines"],
+                           "variant": ["tile", "persistent"][k["variant"]],
                            "tflops": round(k["flops"] / (k["avg_ms"] * 1e-3) / 1e12, 4),
                            "gbs": round(k["bytes"] / (k["avg_ms"] * 1e-3) / 1e9, 1)} for k in kinds]}
     try:

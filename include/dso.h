@@ -134,10 +134,14 @@ dso_status dso_scheme_coefficients(int order, int scheme, int* n_a, int* n_b, do
  * per kind of pass: axis, flags (bit 0 inverse FFT first, bit 1 forward FFT,
  * bit 2 kinetic phase + inverse FFT, bit 8 one potential unitary, bit 9 a
  * second one), surfaces staged per tile, launches per time step and the
- * average duration of one launch in milliseconds.  At most max_kinds kinds
- * are written; *n_kinds receives the number of kinds.  Synchronises. */
+ * average duration of one launch in milliseconds, and the tile line count
+ * and kernel variant (0 one CTA per tile, 1 persistent with a tile queue)
+ * the autotuner chose.  At most max_kinds kinds are written; *n_kinds
+ * receives the number of kinds.  Any output array may be NULL.
+ * Synchronises. */
 dso_status dso_profile_steps(dso_ctx* ctx, double dt, int nsteps, int max_kinds, int* n_kinds, int* axis,
-                             int* flags, int* surfaces, int* launches_per_step, double* avg_ms);
+                             int* flags, int* surfaces, int* launches_per_step, double* avg_ms,
+                             int* tile_lines, int* variant);
 
 /* Number of kernel launches this context has issued since creation
  * (diagnostics: counts each launch of the library's own kernels, including

@@ -61,7 +61,7 @@ def load(path: str = LIB):
         "dso_get_psi": (i32, [vp, vp, i32]),
         "dso_observables": (i32, [vp, pd, pd, pd]),
         "dso_scheme_coefficients": (i32, [i32, i32, pi, pi, pd, pd, pi, pi, pi, pi]),
-        "dso_profile_steps": (i32, [vp, dbl, i32, i32, pi, pi, pi, pi, pi, pd]),
+        "dso_profile_steps": (i32, [vp, dbl, i32, i32, pi, pi, pi, pi, pi, pd, pi, pi]),
         "dso_launch_count": (i64, [vp]),
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
@@ -185,12 +185,12 @@ def dso_profile_steps(ctx, dt, nsteps, max_kinds=16):
     avg_ms (CUDA events around every launch on the context's stream)."""
     lib = load()
     nk = ctypes.c_int()
-    ax, fl, sv, cnt = [(ctypes.c_int * max_kinds)() for _ in range(4)]
+    ax, fl, sv, cnt, gl, var = [(ctypes.c_int * max_kinds)() for _ in range(6)]
     ms = (ctypes.c_double * max_kinds)()
-    _check(lib.dso_profile_steps(ctx, float(dt), int(nsteps), max_kinds, ctypes.byref(nk), ax, fl, sv, cnt, ms),
-           "dso_profile_steps")
-    return [dict(axis=ax[k], flags=fl[k], surfaces=sv[k], launches_per_step=cnt[k], avg_ms=ms[k])
-            for k in range(min(nk.value, max_kinds))]
+    _check(lib.dso_profile_steps(ctx, float(dt), int(nsteps), max_kinds, ctypes.byref(nk), ax, fl, sv, cnt, ms,
+                                 gl, var), "dso_profile_steps")
+    return [dict(axis=ax[k], flags=fl[k], surfaces=sv[k], launches_per_step=cnt[k], avg_ms=ms[k],
+                 tile_lines=gl[k], variant=var[k]) for k in range(min(nk.value, max_kinds))]
 
 
 def dso_launch_count(ctx) -> int:

@@ -24,7 +24,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/dso.h"
+#include "axis_pass_tma.cuh"
 #include "dso_internal.h"
 
 using namespace dso;
@@ -101,8 +104,11 @@ struct dso_ctx {
   // graph of one middle time step
   cudaGraphExec_t step_exec = nullptr;
   int step_exec_passes = 0;
-  // tile lines per (axis) chosen for this grid
+  // tile lines and kernel variant per (axis, surfaces staged: 1 or S)
   int G[DSO_MAX_DIM][2] = {};
+  int variant[DSO_MAX_DIM][2] = {};
+  unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
+  int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
   int64_t launches = 0;
 };
@@ -156,6 +162,38 @@ int choose_G(const dso_ctx* c, int axis, int SV) {
   return (int)G;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &f, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// 5-D FP64 view (re/im, inner i, line position n, outer o, block) of a
+// [blocks][P] complex array for lines along an axis of length L and stride
+// `stride`; box {2, Wi, L, Go, bbox}.
+bool encode_view(CUtensorMap* m, const void* base, long long P, int L, long long stride, long long blocks, int Wi,
+                 int Go, int bbox) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const long long outer = P / ((long long)L * stride);
+  cuuint64_t dims[5] = {2, (cuuint64_t)stride, (cuuint64_t)L, (cuuint64_t)outer, (cuuint64_t)blocks};
+  cuuint64_t strides[4] = {16, (cuuint64_t)(16 * stride), (cuuint64_t)(16 * stride * L), (cuuint64_t)(16 * P)};
+  cuuint32_t box[5] = {2, (cuuint32_t)Wi, (cuuint32_t)L, (cuuint32_t)Go, (cuuint32_t)bbox};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   const int L = (int)c->n[p.axis];
   PassArgs a;
@@ -171,12 +209,37 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.stride = stride;
   a.lines = c->P / L;
   a.S = c->S;
-  a.G = c->G[p.axis][p.SV == 1 ? 0 : 1];
+  const int which = p.SV == 1 ? 0 : 1;
+  a.G = c->G[p.axis][which];
   a.flags = p.flags;
   if (a.G < 1 || (a.G & (a.G - 1)) || a.lines % a.G) return cudaErrorInvalidConfiguration;
+  a.stride_log2 = ilog2(stride);
+  a.G_log2 = ilog2(a.G);
+  a.one = 1.0;
+  a.mz = -0.0;
+  a.ua = p.u1 >= 0 ? p.u1 : 0;
+  a.ub = p.tb >= 0 ? p.tb : 0;
+  a.err = c->err;
   const long long ntiles = (p.SV == c->S) ? a.lines / a.G : (long long)c->S * a.lines / a.G;
+  const int variant = c->variant[p.axis][which];
+  TmaMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  if (variant == 2) {
+    const int Wi = (int)(stride < a.G ? stride : a.G);
+    const int Go = a.G / Wi;
+    const int NP = c->S * (c->S + 1) / 2;
+    bool ok = encode_view(&maps.psi, c->psi, c->P, L, stride, c->S, Wi, Go, p.SV);
+    if (ok && p.u1 >= 0)
+      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)NP * (long long)c->coeffs.a_unq.size(), Wi,
+                       Go, NP);
+    if (ok && p.tb >= 0) {
+      CUtensorMap* m = (p.u1 >= 0) ? &maps.tab2 : &maps.tab;
+      ok = encode_view(m, c->tau, c->P, L, stride, (long long)c->coeffs.b_unq.size(), Wi, Go, 1);
+    }
+    if (!ok) return cudaErrorInvalidConfiguration;
+  }
   c->launches += 1;
-  return launch_axis_pass(L, p.SV, a, ntiles, c->stream);
+  return launch_axis_pass(L, p.SV, variant, a, ntiles, c->queue, &maps, c->stream);
 }
 
 // Pass list of time step `s_first` (true: the first step of a propagate call).
@@ -267,7 +330,8 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 dso_status autotune_tiles(dso_ctx* c) {
   if (c->tuned) return DSO_OK;
   const char* env = getenv("DSO_AUTOTUNE");
-  if (env && env[0] == '0') {
+  const char* fv0 = getenv("DSO_VARIANT");
+  if (env && env[0] == '0' && !(fv0 && fv0[0])) {
     c->tuned = true;
     return DSO_OK;
   }
@@ -301,23 +365,38 @@ dso_status autotune_tiles(dso_ctx* c) {
       for (long long G = 1; G <= gmax && G <= lines; G *= 2)
         if ((SV * G * (L / 8)) % 32 == 0) any_whole = true;
       float best = 1e30f;
-      int bestG = c->G[d][which];
-      for (long long G = 1; G <= gmax && G <= lines && err == cudaSuccess; G *= 2) {
-        if (any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
-        c->G[d][which] = (int)G;
-        err = run_pass(c, p);  // warm-up
-        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_pass(c, p);
-        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        if (err == cudaSuccess && ms < best) {
-          best = ms;
-          bestG = (int)G;
+      int bestG = c->G[d][which], bestV = c->variant[d][which];
+      // DSO_VARIANT=v restricts the search to one kernel variant (testing)
+      const char* fv = getenv("DSO_VARIANT");
+      const int only = (fv && fv[0] >= '0' && fv[0] <= '2') ? fv[0] - '0' : -1;
+      for (int var = 0; var < 3 && err == cudaSuccess; ++var) {
+        if (only >= 0 && var != only) continue;
+        for (long long G = 1; G <= gmax && G <= lines && err == cudaSuccess; G *= 2) {
+          if (any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
+          if (var == 1 && !axis_pass_pq_supported(L, SV, (int)G)) continue;
+          if (var == 2 && !axis_pass_tma_supported(L, SV, (int)G)) continue;
+          c->G[d][which] = (int)G;
+          c->variant[d][which] = var;
+          err = run_pass(c, p);  // warm-up
+          if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+          for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_pass(c, p);
+          if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+          if (err == cudaSuccess && ms < best) {
+            best = ms;
+            bestG = (int)G;
+            bestV = var;
+          }
+          const char* vb = getenv("DSO_TUNE_VERBOSE");
+          if (vb && vb[0] == '1' && err == cudaSuccess)
+            fprintf(stderr, "dso autotune: axis %d SV %d flags %d variant %d G %lld: %.2f us\n", d, SV, p.flags, var,
+                    G, ms * 1000.f / 3.f);
         }
       }
       c->G[d][which] = bestG;
+      c->variant[d][which] = bestV;
     }
   }
   c->psi = keep;
@@ -402,6 +481,8 @@ void dso_destroy(dso_ctx* c) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   drop_model(c);
+  dfree(c->queue);
+  dfree(c->err);
   for (auto& t : c->tw) dfree(t);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -467,10 +548,19 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   CK(cudaMemcpyAsync(c->V, V, count * sizeof(double), where == DSO_HOST ? cudaMemcpyHostToDevice
                                                                          : cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMalloc(&c->psi, (size_t)S * c->P * sizeof(double2)));
+  if (!c->queue) {
+    CK(cudaMalloc(&c->queue, 2 * sizeof(unsigned)));
+    CK(cudaMemsetAsync(c->queue, 0, 2 * sizeof(unsigned), c->stream));
+  }
+  if (!c->err) {
+    CK(cudaMalloc(&c->err, sizeof(int)));
+    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   for (int d = 0; d < c->D; ++d) {
     c->G[d][0] = choose_G(c, d, 1);
     c->G[d][1] = choose_G(c, d, S);
+    c->variant[d][0] = c->variant[d][1] = 0;
   }
   c->have_V = true;
   return DSO_OK;
@@ -559,11 +649,29 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
   return DSO_OK;
 }
 
+// A kernel whose bounded wait gave up leaves a code in c->err; report it at
+// the next synchronising call.
+static dso_status check_device_flag(dso_ctx* c) {
+  if (!c->err) return DSO_OK;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h != 0) {
+    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    return fail(DSO_ETIMEOUT, "a kernel's bounded wait for its tile copy gave up (code " + std::to_string(h) + ")");
+  }
+  return DSO_OK;
+}
+
 dso_status dso_get_psi(dso_ctx* c, void* out, int where) {
   if (!c || !out) return fail(DSO_EINVAL, "null argument");
   if (!c->have_psi) return fail(DSO_ESTATE, "wavefunction not set");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
   DeviceGuard g(c->device);
+  if (where == DSO_HOST) {
+    dso_status fs = check_device_flag(c);
+    if (fs != DSO_OK) return fs;
+  }
   const size_t bytes = (size_t)c->S * c->P * sizeof(double2);
   CK(cudaMemcpyAsync(out, c->psi, bytes, where == DSO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                      c->stream));
@@ -648,7 +756,7 @@ dso_status dso_scheme_coefficients(int order, int scheme, int* n_a, int* n_b, do
 }
 
 dso_status dso_profile_steps(dso_ctx* c, double dt, int nsteps, int max_kinds, int* n_kinds, int* axis, int* flags,
-                             int* surfaces, int* launches_per_step, double* avg_ms) {
+                             int* surfaces, int* launches_per_step, double* avg_ms, int* tile_lines, int* variant) {
   dso_status st = check_ready(c);
   if (st != DSO_OK) return st;
   if (!std::isfinite(dt) || dt == 0.0 || nsteps < 1) return fail(DSO_EINVAL, "need finite dt != 0 and nsteps >= 1");
@@ -713,6 +821,9 @@ dso_status dso_profile_steps(dso_ctx* c, double dt, int nsteps, int max_kinds, i
     if (surfaces) surfaces[k] = kinds[k].sv;
     if (launches_per_step) launches_per_step[k] = kinds[k].count;
     if (avg_ms) avg_ms[k] = kinds[k].ms / ((double)kinds[k].count * nsteps);
+    const int which = kinds[k].sv == 1 ? 0 : 1;
+    if (tile_lines) tile_lines[k] = c->G[kinds[k].axis][which];
+    if (variant) variant[k] = c->variant[kinds[k].axis][which];
   }
   return DSO_OK;
 }
@@ -737,12 +848,27 @@ int axis_pass_max_tile_lines(int L, int SV) {
   return g < 1 ? 1 : g;
 }
 
-cudaError_t launch_axis_pass(int L, int SV, const PassArgs& a, long long ntiles, cudaStream_t st) {
+bool axis_pass_tma_supported(int L, int SV, int G) {
+  if (!axis_pass_supported(L, SV) || L > 256) return false;
+  const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
+  const long long smem = (long long)(SV + np) * G * L * 16 + (long long)L * 16 + 192;
+  return SV * G * (L / 8) <= 256 && smem <= 220 * 1024 && encode_fn() != nullptr;
+}
+
+bool axis_pass_pq_supported(int L, int SV, int G) {
+  if (!axis_pass_supported(L, SV)) return false;
+  const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
+  const long long smem = (long long)(2 * SV + np) * G * L * 16;
+  return SV * G * (L / 8) <= 256 && smem <= 200 * 1024;
+}
+
+cudaError_t launch_axis_pass(int L, int SV, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                             const TmaMaps* maps, cudaStream_t st) {
   switch (SV) {
-    case 1: return launch_axis_pass_sv1(L, a, ntiles, st);
-    case 2: return launch_axis_pass_sv2(L, a, ntiles, st);
-    case 3: return launch_axis_pass_sv3(L, a, ntiles, st);
-    case 4: return launch_axis_pass_sv4(L, a, ntiles, st);
+    case 1: return launch_axis_pass_sv1(L, variant, a, ntiles, queue, maps, st);
+    case 2: return launch_axis_pass_sv2(L, variant, a, ntiles, queue, maps, st);
+    case 3: return launch_axis_pass_sv3(L, variant, a, ntiles, queue, maps, st);
+    case 4: return launch_axis_pass_sv4(L, variant, a, ntiles, queue, maps, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -9,6 +9,8 @@
 
 #include "pass_args.h"
 
+#include <cuda.h>
+
 #define DSO_OBS_COLS 6  // up to 4 populations, <V>, <T>
 
 namespace dso {
@@ -26,12 +28,25 @@ Coeffs build_coefficients(int order, int scheme);
 // Axis-pass launch: L = line length, SV = surfaces staged per tile.
 bool axis_pass_supported(int L, int SV);
 int axis_pass_max_tile_lines(int L, int SV);  // largest G allowed by the thread bound
-cudaError_t launch_axis_pass(int L, int SV, const PassArgs& args, long long ntiles, cudaStream_t st);
+struct TmaMaps;
+// variant 0: one CTA per tile (axis_pass.cuh); variant 1: persistent CTAs
+// with a tile queue and cp.async prefetch (axis_pass_pq.cuh), which needs
+// `queue` (two zeroed unsigned counters owned by the caller's context);
+// variant 2: one CTA per tile with TMA tile and table movement
+// (axis_pass_tma.cuh), which needs the tensor maps in `maps`.
+cudaError_t launch_axis_pass(int L, int SV, int variant, const PassArgs& args, long long ntiles, unsigned* queue,
+                             const TmaMaps* maps, cudaStream_t st);
+bool axis_pass_pq_supported(int L, int SV, int G);
+bool axis_pass_tma_supported(int L, int SV, int G);
 // per-SV launchers (one translation unit each)
-cudaError_t launch_axis_pass_sv1(int L, const PassArgs& a, long long ntiles, cudaStream_t st);
-cudaError_t launch_axis_pass_sv2(int L, const PassArgs& a, long long ntiles, cudaStream_t st);
-cudaError_t launch_axis_pass_sv3(int L, const PassArgs& a, long long ntiles, cudaStream_t st);
-cudaError_t launch_axis_pass_sv4(int L, const PassArgs& a, long long ntiles, cudaStream_t st);
+cudaError_t launch_axis_pass_sv1(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                                 const TmaMaps* maps, cudaStream_t st);
+cudaError_t launch_axis_pass_sv2(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                                 const TmaMaps* maps, cudaStream_t st);
+cudaError_t launch_axis_pass_sv3(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                                 const TmaMaps* maps, cudaStream_t st);
+cudaError_t launch_axis_pass_sv4(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                                 const TmaMaps* maps, cudaStream_t st);
 
 // Operator tables (tables.cu).
 // Twiddles exp(-2 pi i m / L), m = 0..L-1, computed on the host in long

@@ -23,6 +23,13 @@ struct PassArgs {
   int S;                   // surfaces
   int G;                   // lines per surface in one tile (power of two)
   int flags;
+  int stride_log2;         // log2(stride); every stride is a power of two
+  int G_log2;              // log2(G)
+  double one;              // 1.0 and -0.0, passed at run time so that adds and
+  double mz;               // multiplies can be issued as FMAs (axis_pass.cuh)
+  int ua;                  // unique-coefficient index of U1 (TMA variant)
+  int ub;                  // unique-coefficient index of tau (TMA variant)
+  int* err;                // device flag set when a bounded wait gives up
 };
 
 }  // namespace dso

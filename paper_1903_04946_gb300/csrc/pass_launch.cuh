@@ -2,6 +2,8 @@
 #pragma once
 
 #include "axis_pass.cuh"
+#include "axis_pass_pq.cuh"
+#include "axis_pass_tma.cuh"
 #include "dso_internal.h"
 
 namespace dso {
@@ -24,22 +26,89 @@ cudaError_t launch_one(const PassArgs& a, long long ntiles, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Shared memory of the persistent variant: two psi tile buffers and one
+// table buffer (S(S+1)/2 potential entries, or one kinetic phase, per point).
+inline size_t pq_smem_bytes(int L, int SV, int G) {
+  const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
+  return (size_t)(2 * SV + np) * G * L * sizeof(double2);
+}
+
+template <int L, int SV>
+cudaError_t launch_pq(const PassArgs& a, long long ntiles, unsigned* queue, cudaStream_t st) {
+  static bool attr_set[64] = {};
+  static int nsm[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const int threads = SV * a.G * (L / 8);
+  const size_t smem = pq_smem_bytes(L, SV, a.G);
+  if (threads > 256 || smem > 200 * 1024 || !queue) return cudaErrorInvalidConfiguration;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(axis_pass_pq_kernel<L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, axis_pass_pq_kernel<L, SV>, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)per_sm * nsm[dev];
+  if (grid > ntiles) grid = ntiles;
+  axis_pass_pq_kernel<L, SV><<<(unsigned)grid, threads, smem, st>>>(a, queue);
+  return cudaGetLastError();
+}
+
+template <int L, int SV>
+cudaError_t launch_tma(const PassArgs& a, const TmaMaps* maps, long long ntiles, cudaStream_t st) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const int threads = SV * a.G * (L / 8);
+  const size_t smem = tma_smem_bytes<L, SV>(a.G);
+  if (threads > 256 || smem > 220 * 1024 || !maps) return cudaErrorInvalidConfiguration;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(axis_pass_tma_kernel<L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         220 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  axis_pass_tma_kernel<L, SV><<<(unsigned)ntiles, threads, smem, st>>>(a, *maps);
+  return cudaGetLastError();
+}
+
+template <int L, int SV>
+cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, unsigned* queue, const TmaMaps* maps,
+                           cudaStream_t st) {
+  if (variant == 1) {
+    if constexpr (SV * L / 8 <= 256) return launch_pq<L, SV>(a, ntiles, queue, st);
+    return cudaErrorInvalidConfiguration;
+  }
+  if (variant == 2) {
+    if constexpr (L <= 256 && SV * L / 8 <= 256) return launch_tma<L, SV>(a, maps, ntiles, st);
+    return cudaErrorInvalidConfiguration;
+  }
+  return launch_one<L, SV>(a, ntiles, st);
+}
+
 template <int SV>
-cudaError_t launch_by_length(int L, const PassArgs& a, long long ntiles, cudaStream_t st) {
+cudaError_t launch_by_length(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                             const TmaMaps* maps, cudaStream_t st) {
   switch (L) {
-    case 8: return launch_one<8, SV>(a, ntiles, st);
-    case 16: return launch_one<16, SV>(a, ntiles, st);
-    case 32: return launch_one<32, SV>(a, ntiles, st);
-    case 64: return launch_one<64, SV>(a, ntiles, st);
-    case 128: return launch_one<128, SV>(a, ntiles, st);
-    case 256: return launch_one<256, SV>(a, ntiles, st);
-    case 512: return launch_one<512, SV>(a, ntiles, st);
-    case 1024: return launch_one<1024, SV>(a, ntiles, st);
+    case 8: return launch_variant<8, SV>(variant, a, ntiles, queue, maps, st);
+    case 16: return launch_variant<16, SV>(variant, a, ntiles, queue, maps, st);
+    case 32: return launch_variant<32, SV>(variant, a, ntiles, queue, maps, st);
+    case 64: return launch_variant<64, SV>(variant, a, ntiles, queue, maps, st);
+    case 128: return launch_variant<128, SV>(variant, a, ntiles, queue, maps, st);
+    case 256: return launch_variant<256, SV>(variant, a, ntiles, queue, maps, st);
+    case 512: return launch_variant<512, SV>(variant, a, ntiles, queue, maps, st);
+    case 1024: return launch_variant<1024, SV>(variant, a, ntiles, queue, maps, st);
     case 2048:
-      if constexpr (SV * 2048 <= 8192) return launch_one<2048, SV>(a, ntiles, st);
+      if constexpr (SV * 2048 <= 8192) return launch_variant<2048, SV>(variant, a, ntiles, queue, maps, st);
       break;
     case 4096:
-      if constexpr (SV * 4096 <= 8192) return launch_one<4096, SV>(a, ntiles, st);
+      if constexpr (SV * 4096 <= 8192) return launch_variant<4096, SV>(variant, a, ntiles, queue, maps, st);
       break;
     default: break;
   }

@@ -2,7 +2,8 @@
 #include "pass_launch.cuh"
 
 namespace dso {
-cudaError_t launch_axis_pass_sv1(int L, const PassArgs& a, long long ntiles, cudaStream_t st) {
-  return launch_by_length<1>(L, a, ntiles, st);
+cudaError_t launch_axis_pass_sv1(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
+                                   const TmaMaps* maps, cudaStream_t st) {
+  return launch_by_length<1>(L, variant, a, ntiles, queue, maps, st);
 }
 }  // namespace dso
