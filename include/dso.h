@@ -93,9 +93,11 @@ dso_status dso_set_masses(dso_ctx* ctx, const double* m);
 dso_status dso_load_potential(dso_ctx* ctx, int S, const double* V, int where);
 
 /* Composition of Sec. II D-F: order in {2,4,6,8,10}; scheme DSO_TRIPLE_JUMP
- * or DSO_SUZUKI; elementary must be DSO_VTV (Eq. (so_VTV): V acts first and
- * last; DSO_TVT is not part of this build); prune must be 1 (the
- * coefficients of Eq. (merging_splitting_coeff_b_zero)). */
+ * or DSO_SUZUKI; elementary DSO_VTV (Eq. (so_VTV): the potential acts first
+ * and last, with the a~ coefficients) or DSO_TVT (Eq. (so_TVT): the kinetic
+ * step acts first and last and takes the a~ coefficients, the potential the
+ * b~); prune must be 1 (the coefficients of Eq.
+ * (merging_splitting_coeff_b_zero)). */
 dso_status dso_set_scheme(dso_ctx* ctx, int order, int scheme, int elementary, int prune);
 
 /* Set psi (complex128, [S][grid]) from host or device memory. */
@@ -105,7 +107,8 @@ dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);
  * non-negative integer within 1e-9 relative, else DSO_EINVAL).  Each step
  * applies U_V(a~_1 dt) U_T(b~_1 dt) ... U_T(b~_{N_B} dt) U_V(a~_{N_B+1} dt)
  * in the order of the general split-operator product of Sec. II E.
- * Asynchronous on the context's stream. */
+ * Asynchronous on the context's stream.  For DSO_TVT the roles of U_V and
+ * U_T are exchanged. */
 dso_status dso_propagate(dso_ctx* ctx, double t, double dt);
 
 /* Copy psi (complex128, [S][grid]) to host or device memory.  A host copy
@@ -133,7 +136,7 @@ dso_status dso_scheme_coefficients(int order, int scheme, int* n_a, int* n_b, do
  * CUDA event pair around every kernel on the context's stream, then report
  * per kind of pass: axis, flags (bit 0 inverse FFT first, bit 1 forward FFT,
  * bit 2 kinetic phase + inverse FFT, bit 8 one potential unitary, bit 9 a
- * second one), surfaces staged per tile, launches per time step and the
+ * second one, bit 10 a second kinetic phase), surfaces staged per tile, launches per time step and the
  * average duration of one launch in milliseconds, and the tile line count
  * and kernel variant (0 one CTA per tile, 1 persistent with a tile queue)
  * the autotuner chose.  At most max_kinds kinds are written; *n_kinds

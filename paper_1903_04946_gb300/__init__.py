@@ -223,13 +223,13 @@ class Context:
     """Owns one dso context; a convenience holder over the functions above."""
 
     def __init__(self, problem=None, device: int = 0, stream=None, order: int = 2,
-                 scheme: int = DSO_TRIPLE_JUMP):
-        self.ctx = dso_create(device, DSO_FP64, stream)
+                 scheme: int = DSO_TRIPLE_JUMP, elementary: int = DSO_VTV, precision: int = DSO_FP64):
+        self.ctx = dso_create(device, precision, stream)
         self.S = None
         self.shape = None
         if problem is not None:
             self.load_problem(problem)
-            dso_set_scheme(self.ctx, order, scheme)
+            dso_set_scheme(self.ctx, order, scheme, elementary)
 
     def load_problem(self, pr):
         dso_set_grid(self.ctx, pr.n, pr.qmin, pr.qmax)

@@ -301,14 +301,18 @@ __device__ __forceinline__ void apply_potential(double2* sm, const double2* __re
   __syncthreads();
 }
 
+// `scale` multiplies the phase (1 for the first kinetic table; P for a second
+// one, whose 1/P factor belongs to an inverse FFT that does not run twice).
 template <int L>
 __device__ __forceinline__ void apply_kinetic(double2* sm, const double2* __restrict__ tau, const TileGeom& tg,
-                                              int G, int SVl, long long stride, int tid, int nthr, const DPK& dk) {
+                                              int G, int SVl, long long stride, int tid, int nthr, const DPK& dk,
+                                              double scale = 1.0) {
   const int tile_pts = G * L;
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
-    const double2 t = __ldg(&tau[tg.addr(g, n, L, stride)]);
+    double2 t = __ldg(&tau[tg.addr(g, n, L, stride)]);
+    if (scale != 1.0) t = make_double2(dmul(t.x, scale, dk), dmul(t.y, scale, dk));
     const int off = g * L + n;
     for (int s = 0; s < SVl; ++s) {
       double2* p = &sm[(size_t)s * tile_pts + off];
@@ -371,6 +375,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   if (a.flags & PASS_T) {
     __syncthreads();
     apply_kinetic<L>(sm, a.tau, tg, G, SV, a.stride, tid, nthr, dk);
+    if (a.tau2) apply_kinetic<L>(sm, a.tau2, tg, G, SV, a.stride, tid, nthr, dk, a.tau2_scale);
     fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr, dk);
   }
   __syncthreads();

@@ -235,6 +235,19 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
         }
       }
       __syncthreads();
+      if (a.tau2) {  // second kinetic phase of a step boundary, from global memory
+#pragma unroll 1
+        for (int e = tid; e < tile_pts; e += nthr) {
+          const int g = e / L, n = e - (e / L) * L;
+          double2 ph = __ldg(&a.tau2[t.tg.addr(g, n, L, a.stride)]);
+          ph = make_double2(dmul(ph.x, a.tau2_scale, dk), dmul(ph.y, a.tau2_scale, dk));
+          for (int s = 0; s < SV; ++s) {
+            double2* p = &x[(size_t)s * tile_pts + e];
+            *p = cmul(*p, ph, dk);
+          }
+        }
+        __syncthreads();
+      }
       fft_lines_pq<L, true>(x, a.tw, wreg, nslots, tid, nthr, dk);
     }
     __syncthreads();

@@ -337,6 +337,23 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
       }
     }
     __syncthreads();
+    if (a.tau2) {  // second kinetic phase of a step boundary, from global memory
+      const int Wi = 1 << Wi_log2;
+      for (int e = tid; e < tile_pts; e += nthr) {
+        const int i = e & (Wi - 1);
+        const int n = (e >> Wi_log2) & (L - 1);
+        const int o = e >> (Wi_log2 + Plan<L>::log2L);
+        const long long gi = (((tg.o0 + o) * L + n) << a.stride_log2) + tg.i0 + i;
+        double2 ph = __ldg(&a.tau2[gi]);
+        ph = make_double2(dmul(ph.x, a.tau2_scale, dk), dmul(ph.y, a.tau2_scale, dk));
+#pragma unroll
+        for (int s = 0; s < SV; ++s) {
+          double2* p = &x[(size_t)s * tile_pts + e];
+          *p = cmul(*p, ph, dk);
+        }
+      }
+      __syncthreads();
+    }
     tma_fft<L, true>(x, tws, G, Wi_log2, nslots, tid, nthr, dk);
   }
   // make the generic-proxy writes visible to the bulk store, then store

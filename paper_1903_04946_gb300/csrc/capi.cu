@@ -45,9 +45,21 @@ struct Pass {
   int axis;
   int SV;
   int flags;
-  int u1, u2;  // unique-a table indices or -1
-  int tb;      // unique-b table index or -1
+  int u1 = -1, u2 = -1;  // potential table indices (first, second) or -1
+  int tb = -1, tb2 = -1;  // kinetic table indices (first, second) or -1
 };
+
+Pass mkpass(int axis, int SV, int flags, int u1 = -1, int u2 = -1, int tb = -1, int tb2 = -1) {
+  Pass p;
+  p.axis = axis;
+  p.SV = SV;
+  p.flags = flags;
+  p.u1 = u1;
+  p.u2 = u2;
+  p.tb = tb;
+  p.tb2 = tb2;
+  return p;
+}
 
 struct DeviceGuard {
   int prev = -1;
@@ -86,7 +98,7 @@ struct dso_ctx {
   double2* psi = nullptr;    // [S][P]
   bool have_V = false, have_psi = false;
   // scheme
-  int order = 2, scheme = DSO_TRIPLE_JUMP;
+  int order = 2, scheme = DSO_TRIPLE_JUMP, elementary = DSO_VTV;
   Coeffs coeffs;
   bool have_coeffs = false;
   // tables for one dt
@@ -94,7 +106,8 @@ struct dso_ctx {
   double tables_dt = 0.0;
   double2* Utab = nullptr;   // [na][S(S+1)/2][P]
   double2* tau = nullptr;    // [nb][P]
-  double* tau_a = nullptr;   // [na] a_unq * dt
+  double* tau_a = nullptr;   // [na] potential coefficient * dt
+  int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
   double2* tw[13] = {};      // per log2 L
   // observables
   double* Tax = nullptr;     // per-axis p^2 / (2 m_d), concatenated
@@ -202,6 +215,8 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.U1 = p.u1 >= 0 ? c->Utab + (size_t)p.u1 * NP * c->P : nullptr;
   a.U2 = p.u2 >= 0 ? c->Utab + (size_t)p.u2 * NP * c->P : nullptr;
   a.tau = p.tb >= 0 ? c->tau + (size_t)p.tb * c->P : nullptr;
+  a.tau2 = p.tb2 >= 0 ? c->tau + (size_t)p.tb2 * c->P : nullptr;
+  a.tau2_scale = (double)c->P;
   a.tw = c->tw[ilog2(L)];
   a.P = c->P;
   long long stride = 1;
@@ -230,11 +245,10 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
     const int NP = c->S * (c->S + 1) / 2;
     bool ok = encode_view(&maps.psi, c->psi, c->P, L, stride, c->S, Wi, Go, p.SV);
     if (ok && p.u1 >= 0)
-      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)NP * (long long)c->coeffs.a_unq.size(), Wi,
-                       Go, NP);
+      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)NP * (long long)c->n_vtab, Wi, Go, NP);
     if (ok && p.tb >= 0) {
       CUtensorMap* m = (p.u1 >= 0) ? &maps.tab2 : &maps.tab;
-      ok = encode_view(m, c->tau, c->P, L, stride, (long long)c->coeffs.b_unq.size(), Wi, Go, 1);
+      ok = encode_view(m, c->tau, c->P, L, stride, (long long)c->n_ttab, Wi, Go, 1);
     }
     if (!ok) return cudaErrorInvalidConfiguration;
   }
@@ -242,35 +256,85 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   return launch_axis_pass(L, p.SV, variant, a, ntiles, c->queue, &maps, c->stream);
 }
 
-// Pass list of time step `s_first` (true: the first step of a propagate call).
+// Pass lists.  VTV (Eq. (so_VTV)): the potential acts first and last, with
+// tables indexed by I^a and kinetic tables by I^b.  TVT (Eq. (so_TVT)): the
+// kinetic step acts first and last, with kinetic tables indexed by I^a and
+// potential tables by I^b.  The list of a middle step is the same for every
+// step after the first, so it is captured once in a CUDA graph.
+//
+// VTV, D >= 2:  [I0 V F0] [F1..] [F_{D-1} T I_{D-1}] [..I1] per substep,
+//   final [I0 V]; at step boundaries the last V of a step and the first of
+//   the next share one pass.
+// VTV, D = 1:   [V F0 T I0] per substep, final [V].
+// TVT, D >= 2:  first step starts with a standalone [F0]; every potential
+//   action is [I0 V F0]; the last kinetic action of a step and the first of
+//   the next share one kinetic pass; final kinetic action then [I0].
+// TVT, D = 1:   [F0 T I0], then [V F0 T I0] per substep; the final pass is
+//   [V F0 T I0] with the step's last coefficients.
+void t_action(const dso_ctx* c, std::vector<Pass>& out, bool standalone_f0, int tb, int tb2) {
+  const int D = c->D;
+  if (standalone_f0) out.push_back(mkpass(0, 1, PASS_FWD));
+  for (int d = 1; d <= D - 2; ++d) out.push_back(mkpass(d, 1, PASS_FWD));
+  out.push_back(mkpass(D - 1, 1, PASS_FWD | PASS_T, -1, -1, tb, tb2));
+  for (int d = D - 2; d >= 1; --d) out.push_back(mkpass(d, 1, PASS_INV_FIRST));
+}
+
 std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
   std::vector<Pass> out;
+  const std::vector<int>& ia = c->coeffs.ia;
+  const std::vector<int>& ib = c->coeffs.ib;
   const int NB = (int)c->coeffs.b.size();
-  const int last = (int)c->coeffs.a.size() - 1;
+  const int last = (int)c->coeffs.a.size() - 1;  // = NB
   const int D = c->D;
-  for (int j = 0; j < NB; ++j) {
-    int u1 = c->coeffs.ia[j], u2 = -1;
-    if (j == 0 && !first) {
-      u1 = c->coeffs.ia[last];
-      u2 = c->coeffs.ia[0];
+  if (c->elementary == DSO_VTV) {
+    for (int j = 0; j < NB; ++j) {
+      int u1 = ia[j], u2 = -1;
+      if (j == 0 && !first) {
+        u1 = ia[last];
+        u2 = ia[0];
+      }
+      if (D == 1) {
+        out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, u1, u2, ib[j]));
+        continue;
+      }
+      const int inv_first = (j == 0 && first) ? 0 : PASS_INV_FIRST;
+      out.push_back(mkpass(0, c->S, inv_first | PASS_FWD, u1, u2));
+      t_action(c, out, false, ib[j], -1);
     }
-    const int tb = c->coeffs.ib[j];
+    return out;
+  }
+  // TVT: kinetic coefficients a~ (tables by I^a), potential b~ (tables by I^b)
+  for (int j = 0; j < NB; ++j) {
+    const int tb = (j == 0 && !first) ? ia[last] : ia[j];
+    const int tb2 = (j == 0 && !first) ? ia[0] : -1;
+    const int uv = (j == 0) ? (first ? -1 : ib[NB - 1]) : ib[j - 1];
     if (D == 1) {
-      out.push_back(Pass{0, c->S, PASS_FWD | PASS_T, u1, u2, tb});
+      out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, tb, tb2));
       continue;
     }
-    const int inv_first = (j == 0 && first) ? 0 : PASS_INV_FIRST;
-    out.push_back(Pass{0, c->S, inv_first | PASS_FWD, u1, u2, -1});
-    for (int d = 1; d <= D - 2; ++d) out.push_back(Pass{d, 1, PASS_FWD, -1, -1, -1});
-    out.push_back(Pass{D - 1, 1, PASS_FWD | PASS_T, -1, -1, tb});
-    for (int d = D - 2; d >= 1; --d) out.push_back(Pass{d, 1, PASS_INV_FIRST, -1, -1, -1});
+    if (uv >= 0) out.push_back(mkpass(0, c->S, PASS_INV_FIRST | PASS_FWD, uv));
+    t_action(c, out, uv < 0, tb, tb2);
   }
   return out;
 }
 
-Pass final_pass(const dso_ctx* c) {
+std::vector<Pass> final_passes(const dso_ctx* c) {
+  std::vector<Pass> out;
   const int last = (int)c->coeffs.a.size() - 1;
-  return Pass{0, c->S, c->D == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last], -1, -1};
+  const int NB = (int)c->coeffs.b.size();
+  if (c->elementary == DSO_VTV) {
+    out.push_back(mkpass(0, c->S, c->D == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last]));
+    return out;
+  }
+  const int uv = c->coeffs.ib[NB - 1];
+  if (c->D == 1) {
+    out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, c->coeffs.ia[last]));
+    return out;
+  }
+  out.push_back(mkpass(0, c->S, PASS_INV_FIRST | PASS_FWD, uv));
+  t_action(c, out, false, c->coeffs.ia[last], -1);
+  out.push_back(mkpass(0, 1, PASS_INV_FIRST));
+  return out;
 }
 
 #define CK(expr)                                                                                  \
@@ -297,17 +361,23 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   drop_tables(c);
   dso_status st = ensure_twiddles(c);
   if (st != DSO_OK) return st;
-  const int na = (int)c->coeffs.a_unq.size(), nb = (int)c->coeffs.b_unq.size();
+  // VTV: the potential takes the a~ coefficients and the kinetic step the b~;
+  // TVT swaps them.
+  const std::vector<double>& vco = (c->elementary == DSO_VTV) ? c->coeffs.a_unq : c->coeffs.b_unq;
+  const std::vector<double>& tco = (c->elementary == DSO_VTV) ? c->coeffs.b_unq : c->coeffs.a_unq;
+  const int na = (int)vco.size(), nb = (int)tco.size();
   const int NP = c->S * (c->S + 1) / 2;
   CK(cudaMalloc(&c->Utab, (size_t)na * NP * c->P * sizeof(double2)));
   CK(cudaMalloc(&c->tau, (size_t)nb * c->P * sizeof(double2)));
   CK(cudaMalloc(&c->tau_a, (size_t)na * sizeof(double)));
+  c->n_vtab = na;
+  c->n_ttab = nb;
   std::vector<double> ta(na);
-  for (int u = 0; u < na; ++u) ta[u] = c->coeffs.a_unq[u] * dt;
+  for (int u = 0; u < na; ++u) ta[u] = vco[u] * dt;
   CK(cudaMemcpyAsync(c->tau_a, ta.data(), na * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(launch_potential_tables(c->Utab, c->V, c->tau_a, na, c->S, c->P, c->stream));
   c->launches += 1;
-  std::vector<double2> fac = host_kinetic_factors(c->D, c->n, c->qmin, c->qmax, c->mass, c->coeffs.b_unq, dt);
+  std::vector<double2> fac = host_kinetic_factors(c->D, c->n, c->qmin, c->qmax, c->mass, tco, dt);
   double2* dfac = nullptr;
   CK(cudaMalloc(&dfac, fac.size() * sizeof(double2)));
   cudaError_t e = cudaMemcpyAsync(dfac, fac.data(), fac.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
@@ -343,21 +413,25 @@ dso_status autotune_tiles(dso_ctx* c) {
   double2* keep = c->psi;
   c->psi = c->work;
   const int64_t launches = c->launches;
-  for (int d = 0; d < c->D && err == cudaSuccess; ++d) {
-    const int svs[2] = {1, c->S};
-    for (int which = 0; which < 2 && err == cudaSuccess; ++which) {
-      const int SV = svs[which];
-      const bool vpass = (d == 0);
-      if ((SV == c->S) != vpass) continue;  // axis 0 stages all surfaces, the others one
-      Pass p{d, SV, PASS_FWD, -1, -1, -1};
-      if (vpass) {
-        p.u1 = 0;
-        p.flags = (c->D == 1) ? (PASS_FWD | PASS_T) : (PASS_INV_FIRST | PASS_FWD);
-        if (c->D == 1) p.tb = 0;
-      } else if (d == c->D - 1) {
-        p.flags = PASS_FWD | PASS_T;
-        p.tb = 0;
-      }
+  // every kind of pass (axis, surfaces staged) the propagation uses, with a
+  // representative pass of that kind
+  std::vector<Pass> plan = step_passes(c, true);
+  for (const Pass& q : step_passes(c, false)) plan.push_back(q);
+  for (const Pass& q : final_passes(c)) plan.push_back(q);
+  std::vector<Pass> reps;
+  for (const Pass& q : plan) {
+    bool seen = false;
+    for (const Pass& r : reps)
+      if (r.axis == q.axis && (r.SV == 1) == (q.SV == 1)) seen = true;
+    if (!seen) reps.push_back(q);
+  }
+  for (const Pass& rp : reps) {
+    if (err != cudaSuccess) break;
+    Pass p = rp;
+    p.u2 = -1;
+    p.tb2 = -1;
+    const int d = p.axis, SV = p.SV, which = SV == 1 ? 0 : 1;
+    {
       const int L = (int)c->n[d];
       const long long lines = c->P / L;
       const int gmax = axis_pass_max_tile_lines(L, SV);
@@ -570,7 +644,7 @@ dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int
   if (!c) return fail(DSO_EINVAL, "null context");
   if (order < 2 || order > 10 || order % 2) return fail(DSO_EINVAL, "order must be 2, 4, 6, 8 or 10");
   if (scheme != DSO_TRIPLE_JUMP && scheme != DSO_SUZUKI) return fail(DSO_EINVAL, "unknown scheme");
-  if (elementary != DSO_VTV) return fail(DSO_EINVAL, "only the VTV elementary method is part of this build");
+  if (elementary != DSO_VTV && elementary != DSO_TVT) return fail(DSO_EINVAL, "elementary must be DSO_VTV or DSO_TVT");
   if (prune != 1) return fail(DSO_EINVAL, "only pruned coefficients are part of this build");
   try {
     Coeffs cf = build_coefficients(order, scheme);
@@ -580,6 +654,8 @@ dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int
     c->coeffs = cf;
     c->order = order;
     c->scheme = scheme;
+    if (c->elementary != elementary) c->tuned = false;  // other pass kinds
+    c->elementary = elementary;
     c->have_coeffs = true;
   } catch (const std::exception& ex) {
     return fail(DSO_EINVAL, ex.what());
@@ -642,7 +718,7 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
           for (const Pass& p : mid) CK(run_pass(c, p));
       }
     }
-    CK(run_pass(c, final_pass(c)));
+    for (const Pass& p : final_passes(c)) CK(run_pass(c, p));
   } catch (const std::exception& ex) {
     return fail(DSO_EINVAL, ex.what());
   }
@@ -705,7 +781,7 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
   double2* keep = c->psi;
   c->psi = c->work;
   cudaError_t e = cudaSuccess;
-  for (int d = 0; d < c->D && e == cudaSuccess; ++d) e = run_pass(c, Pass{d, 1, PASS_FWD, -1, -1, -1});
+  for (int d = 0; d < c->D && e == cudaSuccess; ++d) e = run_pass(c, mkpass(d, 1, PASS_FWD));
   c->psi = keep;
   CK(e);
   ObsArgs a;
@@ -783,7 +859,7 @@ dso_status dso_profile_steps(dso_ctx* c, double dt, int nsteps, int max_kinds, i
   std::vector<int> kind_of(passes.size());
   for (size_t i = 0; i < passes.size(); ++i) {
     const Pass& p = passes[i];
-    const int f = p.flags | (p.u1 >= 0 ? 256 : 0) | (p.u2 >= 0 ? 512 : 0);
+    const int f = p.flags | (p.u1 >= 0 ? 256 : 0) | (p.u2 >= 0 ? 512 : 0) | (p.tb2 >= 0 ? 1024 : 0);
     int k = -1;
     for (size_t j = 0; j < kinds.size(); ++j)
       if (kinds[j].axis == p.axis && kinds[j].flags == f && kinds[j].sv == p.SV) k = (int)j;

@@ -16,6 +16,8 @@ struct PassArgs {
   const double2* U1;       // [S(S+1)/2][P] potential unitary, or null
   const double2* U2;       // second potential unitary, or null
   const double2* tau;      // [P] kinetic phase (1/P folded in), or null
+  const double2* tau2;     // second kinetic phase (TVT step boundary), or null;
+                           // its folded 1/P is undone by tau2_scale = P (exact)
   const double2* tw;       // [L] exp(-2 pi i m / L), m = 0..L-1
   long long P;             // grid points per surface
   long long stride;        // element stride of the axis (product of later axes)
@@ -30,6 +32,7 @@ struct PassArgs {
   int ua;                  // unique-coefficient index of U1 (TMA variant)
   int ub;                  // unique-coefficient index of tau (TMA variant)
   int* err;                // device flag set when a bounded wait gives up
+  double tau2_scale;       // P: both kinetic tables carry 1/P, one inverse FFT runs
 };
 
 }  // namespace dso

@@ -15,10 +15,11 @@ def require_gpu():
     return dso
 
 
-def gpu_propagate(problem, order, scheme, t, dt, psi=None):
+def gpu_propagate(problem, order, scheme, t, dt, psi=None, elementary="VTV"):
     import paper_1903_04946_gb300 as dso
     sch = dso.DSO_SUZUKI if scheme == "suzuki" else dso.DSO_TRIPLE_JUMP
-    ctx = dso.Context(problem, order=order, scheme=sch)
+    el = dso.DSO_TVT if elementary == "TVT" else dso.DSO_VTV
+    ctx = dso.Context(problem, order=order, scheme=sch, elementary=el)
     try:
         if psi is not None:
             dso.dso_set_psi(ctx.ctx, psi)
@@ -28,9 +29,9 @@ def gpu_propagate(problem, order, scheme, t, dt, psi=None):
         ctx.close()
 
 
-def oracle_propagate(problem, order, scheme, t, dt, psi=None):
+def oracle_propagate(problem, order, scheme, t, dt, psi=None, elementary="VTV"):
     from oracle import propagate as P
-    return P.propagate(problem, t, dt, order=order, scheme=scheme, psi=psi)
+    return P.propagate(problem, t, dt, order=order, scheme=scheme, psi=psi, elementary=elementary)
 
 
 def rel_l2(a, b):

@@ -159,3 +159,31 @@ def test_errors_are_reported(dso):
             dso.dso_load_potential(ctx, 3, np.zeros((6, 4096)))  # S * n > 8192
     finally:
         dso.dso_destroy(ctx)
+
+
+# -- TVT elementary method (Eq. (so_TVT)): kinetic step first and last
+@pytest.mark.parametrize("n,S,order,scheme,nsteps", [
+    ((64, 64, 64), 3, 4, "triple_jump", 2), ((16, 32, 8), 3, 6, "suzuki", 2), ((32, 64), 2, 4, "suzuki", 3),
+    ((1024,), 2, 4, "triple_jump", 3), ((256,), 3, 2, "triple_jump", 1), ((64,), 4, 6, "triple_jump", 2)])
+def test_tvt_parity(dso, n, S, order, scheme, nsteps):
+    if len(n) == 3 and S == 3:
+        pr = synth.pyrazine_like(seed=31, n=n)
+        dt = 2000.0 / 128
+    else:
+        pr = synth.random_coupled(40 + S, n, S, extent=10.0 if len(n) == 1 else 6.0)
+        dt = 0.2
+    ref = oracle_propagate(pr, order, scheme, nsteps * dt, dt, elementary="TVT")
+    out = gpu_propagate(pr, order, scheme, nsteps * dt, dt, elementary="TVT")
+    assert_parity(out, ref)
+
+
+def test_tvt_time_reversible_and_norm(dso):
+    pr = synth.random_coupled(9, (32, 32), 2, extent=6.0)
+    ctx = dso.Context(pr, order=4, scheme=dso.DSO_SUZUKI, elementary=dso.DSO_TVT)
+    ctx.propagate(2.0, 0.25)
+    n1, _, _ = ctx.observables()
+    ctx.propagate(-2.0, -0.25)
+    back = ctx.psi()
+    ctx.close()
+    assert abs(n1 - 1.0) < 1e-13
+    assert rel_l2(back, pr.psi0) < 1e-12

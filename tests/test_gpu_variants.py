@@ -42,3 +42,15 @@ def test_variants_agree_bitwise_or_closely(monkeypatch):
     for o in outs[1:]:
         # same arithmetic in the same order: the variants differ only in data movement
         assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("n,S", [((16, 32, 8), 3), ((256,), 2)])
+def test_variant_parity_tvt(monkeypatch, variant, n, S):
+    require_gpu()
+    monkeypatch.setenv("DSO_VARIANT", variant)
+    pr = synth.pyrazine_like(seed=4, n=n) if len(n) == 3 else synth.random_coupled(3, n, S, extent=12.0)
+    dt = 40.0 if len(n) == 3 else 0.2
+    ref = oracle_propagate(pr, 4, "suzuki", 2 * dt, dt, elementary="TVT")
+    out = gpu_propagate(pr, 4, "suzuki", 2 * dt, dt, elementary="TVT")
+    assert_parity(out, ref)
