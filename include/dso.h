@@ -16,8 +16,9 @@
  *  - atomic units, hbar = 1;
  *  - grid axis d has n[d] points q_k = qmin[d] + k (qmax[d]-qmin[d])/n[d],
  *    k = 0..n[d]-1 (periodic, right endpoint excluded);
- *  - psi is complex128 (interleaved re, im), surface-major
- *    [S][n_0][n_1]...[n_{D-1}], last axis contiguous;
+ *  - psi is complex128 (interleaved re, im) in a DSO_FP64 context and
+ *    complex64 in a DSO_FP32 context, surface-major [S][n_0][n_1]...[n_{D-1}],
+ *    last axis contiguous;
  *  - the potential is real symmetric, passed packed as the upper triangle
  *    [S(S+1)/2][n_0]...[n_{D-1}] float64, pairs (r,c), r <= c, row-major:
  *    (0,0),(0,1),(1,1) for S = 2; (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) for S = 3;
@@ -69,10 +70,14 @@ enum { DSO_VTV = 0, DSO_TVT = 1 };
 #define DSO_MIN_AXIS 8
 #define DSO_MAX_AXIS 4096
 
-/* Create a context on CUDA device `device`.  precision must be DSO_FP64
- * (FP32 storage is not part of this build: DSO_EINVAL).  `cuda_stream` is a
- * cudaStream_t owned by the caller, or NULL to let the context create and
- * own a non-blocking stream.  *out receives the context (NULL on failure). */
+/* Create a context on CUDA device `device`.  precision DSO_FP64 keeps psi,
+ * the operator tables and the FFTs in FP64; DSO_FP32 stores psi and the
+ * tables as complex64 and runs the FFTs in FP32, while the potential phase
+ * angles V a~ dt, the kinetic phases, the composition coefficients and the
+ * norm/energy reductions stay FP64 (tables are rounded to FP32 once).
+ * `cuda_stream` is a cudaStream_t owned by the caller, or NULL to let the
+ * context create and own a non-blocking stream.  *out receives the context
+ * (NULL on failure). */
 dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_stream);
 
 /* Release the context and every device buffer it owns.  NULL is a no-op. */
@@ -100,7 +105,8 @@ dso_status dso_load_potential(dso_ctx* ctx, int S, const double* V, int where);
  * (merging_splitting_coeff_b_zero)). */
 dso_status dso_set_scheme(dso_ctx* ctx, int order, int scheme, int elementary, int prune);
 
-/* Set psi (complex128, [S][grid]) from host or device memory. */
+/* Set psi ([S][grid], complex128 or complex64 by the context's precision)
+ * from host or device memory. */
 dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);
 
 /* Advance psi by time t with step dt (dt may be negative; t/dt must be a
@@ -111,8 +117,8 @@ dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);
  * U_T are exchanged. */
 dso_status dso_propagate(dso_ctx* ctx, double t, double dt);
 
-/* Copy psi (complex128, [S][grid]) to host or device memory.  A host copy
- * synchronises the stream. */
+/* Copy psi ([S][grid], complex128 or complex64 by the context's precision)
+ * to host or device memory.  A host copy synchronises the stream. */
 dso_status dso_get_psi(dso_ctx* ctx, void* out, int where);
 
 /* Observables of Sec. II A on the current psi, in FP64: norm = ||psi||,

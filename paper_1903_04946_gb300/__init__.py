@@ -142,8 +142,12 @@ def dso_set_scheme(ctx, order, scheme=DSO_TRIPLE_JUMP, elementary=DSO_VTV, prune
 
 
 def dso_set_psi(ctx, psi):
+    """psi must have the context's element type (complex128 for DSO_FP64,
+    complex64 for DSO_FP32)."""
     if isinstance(psi, np.ndarray):
-        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        if psi.dtype not in (np.complex64, np.complex128):
+            psi = psi.astype(np.complex128)
+        psi = np.ascontiguousarray(psi)
     p, where = _ptr(psi)
     _check(load().dso_set_psi(ctx, p, where), "dso_set_psi")
 
@@ -225,6 +229,7 @@ class Context:
     def __init__(self, problem=None, device: int = 0, stream=None, order: int = 2,
                  scheme: int = DSO_TRIPLE_JUMP, elementary: int = DSO_VTV, precision: int = DSO_FP64):
         self.ctx = dso_create(device, precision, stream)
+        self.dtype = np.complex64 if precision == DSO_FP32 else np.complex128
         self.S = None
         self.shape = None
         if problem is not None:
@@ -235,15 +240,18 @@ class Context:
         dso_set_grid(self.ctx, pr.n, pr.qmin, pr.qmax)
         dso_set_masses(self.ctx, pr.mass)
         dso_load_potential(self.ctx, pr.S, pr.V)
-        dso_set_psi(self.ctx, pr.psi0)
+        dso_set_psi(self.ctx, np.ascontiguousarray(pr.psi0, dtype=self.dtype))
         self.S = pr.S
         self.shape = (pr.S,) + tuple(pr.n)
 
     def propagate(self, t, dt):
         dso_propagate(self.ctx, t, dt)
 
+    def set_psi(self, psi):
+        dso_set_psi(self.ctx, np.ascontiguousarray(psi, dtype=self.dtype))
+
     def psi(self) -> np.ndarray:
-        out = np.empty(self.shape, dtype=np.complex128)
+        out = np.empty(self.shape, dtype=self.dtype)
         return dso_get_psi(self.ctx, out)
 
     def observables(self):

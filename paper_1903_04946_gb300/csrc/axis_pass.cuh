@@ -20,12 +20,16 @@
 // step 4 in the momentum representation on all axes; the host orders the
 // passes so that this holds.
 //
-// The FP64 path on this GPU is bound by the FP64 pipe (one DFMA per SM
-// sub-partition every 64 cycles for a full warp), so the butterflies are
-// written to minimise FP64 instructions: trivial twiddles (+-1, +-i) cost
-// nothing, the (1 -+ i)/sqrt(2) factors of the radix-8 butterfly fold into
-// FMAs, and everything else (indexing, shared-memory traffic, table loads)
-// runs on other pipes.
+// The FP64 path on this GPU is bound by the FP64 pipe: 2 FP64 lanes per SM
+// per clock, and (measured) 0.50 T instructions/s for DADD, DMUL and for a
+// DFMA with two per-thread register operands, as in these butterflies.  The
+// butterflies are written to minimise FP64 instructions: trivial twiddles
+// (+-1, +-i) cost nothing, the (1 -+ i)/sqrt(2) factors of the radix-8
+// butterfly fold into FMAs, and everything else (indexing, shared-memory
+// traffic, table loads) runs on other pipes.
+//
+// Every routine is generic over the complex type C: double2 for the FP64
+// path, float2 for the FP32 storage-and-FFT mode.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,93 +39,102 @@
 
 namespace dso {
 
-// FP64 arithmetic of the hot path.  On this GPU the FP64 pipe issues DFMA
-// about 1.19x faster than DADD or DMUL (measured: 0.599 vs 0.504 T inst/s),
-// so every add, subtract and multiply is issued as an FMA: a + b = fma(a, 1, b)
-// and a * b = fma(a, b, -0), both exactly rounded like the plain operation.
-// The 1.0 and -0.0 come from the kernel arguments: with literal constants the
-// compiler folds the FMA back into DADD/DMUL.
-struct DPK {
-  double one;  // 1.0 at run time
-  double mz;   // -0.0 at run time
+template <typename C>
+struct CxT;
+template <>
+struct CxT<double2> {
+  using R = double;
 };
-__device__ __forceinline__ double dadd(double a, double b, const DPK& k) { return fma(a, k.one, b); }
-__device__ __forceinline__ double dsub(double a, double b, const DPK& k) { return fma(-b, k.one, a); }
-__device__ __forceinline__ double dmul(double a, double b, const DPK& k) { return fma(a, b, k.mz); }
+template <>
+struct CxT<float2> {
+  using R = float;
+};
+template <typename C>
+using RealT = typename CxT<C>::R;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b, const DPK& k) {
-  return make_double2(fma(a.x, b.x, dmul(-a.y, b.y, k)), fma(a.x, b.y, dmul(a.y, b.x, k)));
+__device__ __forceinline__ double2 mkc(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 mkc(float x, float y) { return make_float2(x, y); }
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 // a * conj(b)
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b, const DPK& k) {
-  return make_double2(fma(a.x, b.x, dmul(a.y, b.y, k)), fma(a.y, b.x, dmul(-a.x, b.y, k)));
+template <typename C>
+__device__ __forceinline__ C cmulc(C a, C b) {
+  return mkc(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b, const DPK& k) {
-  return make_double2(dadd(a.x, b.x, k), dadd(a.y, b.y, k));
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  return mkc(a.x + b.x, a.y + b.y);
 }
-__device__ __forceinline__ double2 csub(double2 a, double2 b, const DPK& k) {
-  return make_double2(dsub(a.x, b.x, k), dsub(a.y, b.y, k));
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+  return mkc(a.x - b.x, a.y - b.y);
 }
-// multiply by -i (forward) or +i (inverse): free, no FP64 instruction
-template <bool INV>
-__device__ __forceinline__ double2 rot_i(double2 a) {
-  return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+template <typename C>
+__device__ __forceinline__ C cscale(C a, RealT<C> s) {
+  return mkc(a.x * s, a.y * s);
+}
+// multiply by -i (forward) or +i (inverse): free, no floating-point instruction
+template <bool INV, typename C>
+__device__ __forceinline__ C rot_i(C a) {
+  return INV ? mkc(-a.y, a.x) : mkc(a.y, -a.x);
 }
 
 // In-place DFT of length 2, 4, 8 with sign -1 (forward) or +1 (INV).
-template <bool INV>
-__device__ __forceinline__ void dft2(double2& a, double2& b, const DPK& k) {
-  double2 t = a;
-  a = cadd(t, b, k);
-  b = csub(t, b, k);
+template <bool INV, typename C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(double2& a0, double2& a1, double2& a2, double2& a3, const DPK& k) {
-  double2 t0 = cadd(a0, a2, k), t1 = csub(a0, a2, k);
-  double2 t2 = cadd(a1, a3, k), t3 = rot_i<INV>(csub(a1, a3, k));
-  a0 = cadd(t0, t2, k);
-  a2 = csub(t0, t2, k);
-  a1 = cadd(t1, t3, k);
-  a3 = csub(t1, t3, k);
+template <bool INV, typename C>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  C t2 = cadd(a1, a3), t3 = rot_i<INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
 }
 
 // 8-point DFT by one radix-2 split into two 4-point DFTs:
 // y_k = E_k + w^k O_k, y_{k+4} = E_k - w^k O_k, w = exp(-+2 pi i / 8).
-template <bool INV>
-__device__ __forceinline__ void dft8(double2* x, const DPK& k) {
-  const double c = 0.70710678118654752440;  // 1/sqrt(2)
-  double2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-  double2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-  dft4<INV>(e0, e1, e2, e3, k);
-  dft4<INV>(o0, o1, o2, o3, k);
+template <bool INV, typename C>
+__device__ __forceinline__ void dft8(C* x) {
+  using R = RealT<C>;
+  const R c = (R)0.70710678118654752440;  // 1/sqrt(2)
+  C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
   // k = 0
-  x[0] = cadd(e0, o0, k);
-  x[4] = csub(e0, o0, k);
+  x[0] = cadd(e0, o0);
+  x[4] = csub(e0, o0);
   // k = 2: w^2 = -+i
-  double2 r2 = rot_i<INV>(o2);
-  x[2] = cadd(e2, r2, k);
-  x[6] = csub(e2, r2, k);
+  C r2 = rot_i<INV>(o2);
+  x[2] = cadd(e2, r2);
+  x[6] = csub(e2, r2);
   // k = 1: w = (1 -+ i)/sqrt(2); w*o = c * u
-  double2 u1 = INV ? make_double2(dsub(o1.x, o1.y, k), dadd(o1.x, o1.y, k))
-                   : make_double2(dadd(o1.x, o1.y, k), dsub(o1.y, o1.x, k));
-  x[1] = make_double2(fma(c, u1.x, e1.x), fma(c, u1.y, e1.y));
-  x[5] = make_double2(fma(-c, u1.x, e1.x), fma(-c, u1.y, e1.y));
+  C u1 = INV ? mkc(o1.x - o1.y, o1.x + o1.y) : mkc(o1.x + o1.y, o1.y - o1.x);
+  x[1] = mkc(fma(c, u1.x, e1.x), fma(c, u1.y, e1.y));
+  x[5] = mkc(fma(-c, u1.x, e1.x), fma(-c, u1.y, e1.y));
   // k = 3: w^3 = (-1 -+ i)/sqrt(2)
-  double2 u3 = INV ? make_double2(-dadd(o3.x, o3.y, k), dsub(o3.x, o3.y, k))
-                   : make_double2(dsub(o3.y, o3.x, k), -dadd(o3.x, o3.y, k));
-  x[3] = make_double2(fma(c, u3.x, e3.x), fma(c, u3.y, e3.y));
-  x[7] = make_double2(fma(-c, u3.x, e3.x), fma(-c, u3.y, e3.y));
+  C u3 = INV ? mkc(-(o3.x + o3.y), o3.x - o3.y) : mkc(o3.y - o3.x, -(o3.x + o3.y));
+  x[3] = mkc(fma(c, u3.x, e3.x), fma(c, u3.y, e3.y));
+  x[7] = mkc(fma(-c, u3.x, e3.x), fma(-c, u3.y, e3.y));
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dftR(double2* x, const DPK& k) {
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dftR(C* x) {
   if constexpr (R == 8) {
-    dft8<INV>(x, k);
+    dft8<INV>(x);
   } else if constexpr (R == 4) {
-    dft4<INV>(x[0], x[1], x[2], x[3], k);
+    dft4<INV>(x[0], x[1], x[2], x[3]);
   } else {
-    dft2<INV>(x[0], x[1], k);
+    dft2<INV>(x[0], x[1]);
   }
 }
 
@@ -157,19 +170,19 @@ __device__ __forceinline__ unsigned warp_lanes_mask(int tid, int nthr) {
 // One Stockham stage of radix R on every line of the tile held in `sm`.
 // Thread-slot s of this thread owns 8 consecutive butterfly inputs' worth of
 // work: 8/R butterflies j = u*(8/R) + beta of line `line`.
-template <int L, int R, bool INV, int K>
-__device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double2* __restrict__ tw,
-                                               int nslots, int tid, int nthr, unsigned wmask, const DPK& dk) {
+template <int L, int R, bool INV, int K, typename C>
+__device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restrict__ tw, int nslots, int tid,
+                                               int nthr, unsigned wmask) {
   constexpr int NB = 8 / R;      // butterflies per slot
   constexpr int Q = L / R;       // butterflies per line
-  double2 v[K][8];
+  C v[K][8];
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     const int gid = s * nthr + tid;
     if (gid < nslots) {
       const int line = gid / (L / 8);
       const int u = gid % (L / 8);
-      const double2* ln = sm + (size_t)line * L;
+      const C* ln = sm + (size_t)line * L;
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
@@ -185,21 +198,21 @@ __device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double
     if (gid < nslots) {
       const int line = gid / (L / 8);
       const int u = gid % (L / 8);
-      double2* ln = sm + (size_t)line * L;
+      C* ln = sm + (size_t)line * L;
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
         const int k = j & (Ls - 1);
-        double2* x = &v[s][beta * R];
+        C* x = &v[s][beta * R];
         if (Ls > 1) {
           const int step = (L / (Ls * R)) * k;
 #pragma unroll
           for (int r = 1; r < R; ++r) {
-            const double2 w = __ldg(&tw[r * step]);
-            x[r] = INV ? cmulc(x[r], w, dk) : cmul(x[r], w, dk);
+            const C w = __ldg(&tw[r * step]);
+            x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
           }
         }
-        dftR<R, INV>(x, dk);
+        dftR<R, INV>(x);
         const int base = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) ln[base + r * Ls] = x[r];
@@ -209,16 +222,15 @@ __device__ __forceinline__ void stockham_stage(double2* sm, int Ls, const double
   stage_sync<L>(wmask);
 }
 
-template <int L, bool INV, int K>
-__device__ __forceinline__ void fft_lines(double2* sm, const double2* __restrict__ tw, int nslots, int tid, int nthr,
-                                          const DPK& dk) {
+template <int L, bool INV, int K, typename C>
+__device__ __forceinline__ void fft_lines(C* sm, const C* __restrict__ tw, int nslots, int tid, int nthr) {
   using PL = Plan<L>;
   const unsigned wmask = warp_lanes_mask(tid, nthr);
-  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr, wmask, dk);
+  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr, wmask);
   int Ls = PL::first;
 #pragma unroll 1
   for (int st = 0; st < PL::n8; ++st) {
-    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr, wmask, dk);
+    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr, wmask);
     Ls *= 8;
   }
 }
@@ -260,10 +272,33 @@ __device__ __forceinline__ void tile_elem(int e, const TileGeom& tg, int& g, int
   g = (o << tg.Wi_log2) | i;
 }
 
-template <int L, int SV>
-__device__ __forceinline__ void apply_potential(double2* sm, const double2* __restrict__ U, const TileGeom& tg,
-                                                int G, long long stride, long long P, int tid, int nthr,
-                                                const DPK& dk) {
+// S x S complex matvec with the packed complex-symmetric unitary (entries
+// in C, products accumulated in C's precision).
+template <int SV, typename C>
+__device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], const C (&x)[SV], C (&y)[SV]) {
+#pragma unroll
+  for (int r = 0; r < SV; ++r) {
+    C acc = mkc((RealT<C>)0, (RealT<C>)0);
+#pragma unroll
+    for (int c = 0; c < SV; ++c) {
+      const int lo = r < c ? r : c, hi = r < c ? c : r;
+      const int k = lo * SV - lo * (lo - 1) / 2 + (hi - lo);
+      if (c == 0) {
+        acc = cmul(u[k], x[c]);
+      } else {
+        acc.x = fma(u[k].x, x[c].x, acc.x);
+        acc.x = fma(-u[k].y, x[c].y, acc.x);
+        acc.y = fma(u[k].x, x[c].y, acc.y);
+        acc.y = fma(u[k].y, x[c].x, acc.y);
+      }
+    }
+    y[r] = acc;
+  }
+}
+
+template <int L, int SV, typename C>
+__device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, const TileGeom& tg, int G,
+                                                long long stride, long long P, int tid, int nthr) {
   constexpr int NP = SV * (SV + 1) / 2;
   const int tile_pts = G * L;
   for (int e = tid; e < tile_pts; e += nthr) {
@@ -271,30 +306,12 @@ __device__ __forceinline__ void apply_potential(double2* sm, const double2* __re
     tile_elem<L>(e, tg, g, n);
     const long long gi = tg.addr(g, n, L, stride);
     const int off = g * L + n;
-    double2 x[SV], y[SV];
+    C x[SV], y[SV], u[NP];
 #pragma unroll
     for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + off];
-    double2 u[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) u[k] = __ldg(&U[(size_t)k * P + gi]);
-#pragma unroll
-    for (int r = 0; r < SV; ++r) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int c = 0; c < SV; ++c) {
-        const int lo = r < c ? r : c, hi = r < c ? c : r;
-        const int k = lo * SV - lo * (lo - 1) / 2 + (hi - lo);
-        if (c == 0) {
-          acc = cmul(u[k], x[c], dk);
-        } else {
-          acc.x = fma(u[k].x, x[c].x, acc.x);
-          acc.x = fma(-u[k].y, x[c].y, acc.x);
-          acc.y = fma(u[k].x, x[c].y, acc.y);
-          acc.y = fma(u[k].y, x[c].x, acc.y);
-        }
-      }
-      y[r] = acc;
-    }
+    matvec_sym<SV>(u, x, y);
 #pragma unroll
     for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + off] = y[s];
   }
@@ -303,20 +320,19 @@ __device__ __forceinline__ void apply_potential(double2* sm, const double2* __re
 
 // `scale` multiplies the phase (1 for the first kinetic table; P for a second
 // one, whose 1/P factor belongs to an inverse FFT that does not run twice).
-template <int L>
-__device__ __forceinline__ void apply_kinetic(double2* sm, const double2* __restrict__ tau, const TileGeom& tg,
-                                              int G, int SVl, long long stride, int tid, int nthr, const DPK& dk,
-                                              double scale = 1.0) {
+template <int L, typename C>
+__device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, const TileGeom& tg, int G, int SVl,
+                                              long long stride, int tid, int nthr, RealT<C> scale = 1) {
   const int tile_pts = G * L;
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
-    double2 t = __ldg(&tau[tg.addr(g, n, L, stride)]);
-    if (scale != 1.0) t = make_double2(dmul(t.x, scale, dk), dmul(t.y, scale, dk));
+    C t = __ldg(&tau[tg.addr(g, n, L, stride)]);
+    if (scale != (RealT<C>)1) t = cscale(t, scale);
     const int off = g * L + n;
     for (int s = 0; s < SVl; ++s) {
-      double2* p = &sm[(size_t)s * tile_pts + off];
-      *p = cmul(*p, t, dk);
+      C* p = &sm[(size_t)s * tile_pts + off];
+      *p = cmul(*p, t);
     }
   }
   __syncthreads();
@@ -330,10 +346,13 @@ struct MaxThreads {
   static constexpr int value = (SV * L / 8 > 256) ? SV * L / 8 : 256;
 };
 
-template <int L, int SV>
+template <int L, int SV, typename C>
 __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(PassArgs a) {
   constexpr int K = 1;
-  extern __shared__ double2 sm[];
+  extern __shared__ __align__(16) unsigned char sm_bytes[];
+  C* sm = reinterpret_cast<C*>(sm_bytes);
+  C* psi = reinterpret_cast<C*>(a.psi);
+  const C* tw = reinterpret_cast<const C*>(a.tw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int G = a.G;
   const int tile_pts = G * L;
@@ -349,7 +368,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
 
   // load
   for (int s = 0; s < SV; ++s) {
-    const double2* src = a.psi + (size_t)(surf0 + s) * a.P;
+    const C* src = psi + (size_t)(surf0 + s) * a.P;
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, tg, g, n);
@@ -359,30 +378,31 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   __syncthreads();
 
   const int nslots = SV * G * (L / 8);
-  const DPK dk{a.one, a.mz};
   // The tile-wide steps (load, potential, kinetic phase, store) walk the tile
   // in address order and end with a block barrier; the FFT stages in between
   // only synchronise the threads of each line.
   if (a.flags & PASS_INV_FIRST) {
-    fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr, dk);
+    fft_lines<L, true, K>(sm, tw, nslots, tid, nthr);
     __syncthreads();
   }
   if (SV > 1) {  // the host sets U1/U2 only for passes that stage all S surfaces
-    if (a.U1) apply_potential<L, SV>(sm, a.U1, tg, G, a.stride, a.P, tid, nthr, dk);
-    if (a.U2) apply_potential<L, SV>(sm, a.U2, tg, G, a.stride, a.P, tid, nthr, dk);
+    if (a.U1) apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U1), tg, G, a.stride, a.P, tid, nthr);
+    if (a.U2) apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U2), tg, G, a.stride, a.P, tid, nthr);
   }
-  if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, a.tw, nslots, tid, nthr, dk);
+  if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, tw, nslots, tid, nthr);
   if (a.flags & PASS_T) {
     __syncthreads();
-    apply_kinetic<L>(sm, a.tau, tg, G, SV, a.stride, tid, nthr, dk);
-    if (a.tau2) apply_kinetic<L>(sm, a.tau2, tg, G, SV, a.stride, tid, nthr, dk, a.tau2_scale);
-    fft_lines<L, true, K>(sm, a.tw, nslots, tid, nthr, dk);
+    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr);
+    if (a.tau2)
+      apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau2), tg, G, SV, a.stride, tid, nthr,
+                       (RealT<C>)a.tau2_scale);
+    fft_lines<L, true, K>(sm, tw, nslots, tid, nthr);
   }
   __syncthreads();
 
   // store
   for (int s = 0; s < SV; ++s) {
-    double2* dst = a.psi + (size_t)(surf0 + s) * a.P;
+    C* dst = psi + (size_t)(surf0 + s) * a.P;
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, tg, g, n);

@@ -35,7 +35,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // of 64-point lines, where each thread's k is fixed for the whole launch).
 template <int L, bool INV>
 __device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const double2 (&w)[8], int nslots, int tid,
-                                                unsigned wmask, const DPK& dk) {
+                                                unsigned wmask) {
   constexpr int Q = L / 8;
   double2 v[8];
   const bool act = tid < nslots;
@@ -50,8 +50,8 @@ __device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const doubl
   if (act) {
     const int k = u & (Ls - 1);
 #pragma unroll
-    for (int r = 1; r < 8; ++r) v[r] = INV ? cmulc(v[r], w[r], dk) : cmul(v[r], w[r], dk);
-    dftR<8, INV>(v, dk);
+    for (int r = 1; r < 8; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
+    dftR<8, INV>(v);
     const int base = (u - k) * 8 + k;
 #pragma unroll
     for (int r = 0; r < 8; ++r) ln[base + r * Ls] = v[r];
@@ -61,18 +61,18 @@ __device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const doubl
 
 template <int L, bool INV>
 __device__ __forceinline__ void fft_lines_pq(double2* sm, const double2* __restrict__ tw, const double2 (&wreg)[8],
-                                             int nslots, int tid, int nthr, const DPK& dk) {
+                                             int nslots, int tid, int nthr) {
   using PL = Plan<L>;
   const unsigned wmask = warp_lanes_mask(tid, nthr);
   if constexpr (L == 64) {
-    stockham_stage<L, 8, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask, dk);
-    stockham8_regtw<L, INV>(sm, 8, wreg, nslots, tid, wmask, dk);
+    stockham_stage<L, 8, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask);
+    stockham8_regtw<L, INV>(sm, 8, wreg, nslots, tid, wmask);
   } else {
-    stockham_stage<L, PL::first, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask, dk);
+    stockham_stage<L, PL::first, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask);
     int Ls = PL::first;
 #pragma unroll 1
     for (int st = 0; st < PL::n8; ++st) {
-      stockham_stage<L, 8, INV, 1>(sm, Ls, tw, nslots, tid, nthr, wmask, dk);
+      stockham_stage<L, 8, INV, 1>(sm, Ls, tw, nslots, tid, nthr, wmask);
       Ls *= 8;
     }
   }
@@ -115,8 +115,7 @@ __device__ __forceinline__ void pq_issue(double2* dst, const double2* src, int c
 }
 
 template <int SV>
-__device__ __forceinline__ void pq_potential(double2* sm, const double2* ub, int tile_pts, int tid, int nthr,
-                                             const DPK& dk) {
+__device__ __forceinline__ void pq_potential(double2* sm, const double2* ub, int tile_pts, int tid, int nthr) {
   constexpr int NP = SV * (SV + 1) / 2;
 #pragma unroll 1
   for (int e = tid; e < tile_pts; e += nthr) {
@@ -125,24 +124,7 @@ __device__ __forceinline__ void pq_potential(double2* sm, const double2* ub, int
     for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + e];
 #pragma unroll
     for (int k = 0; k < NP; ++k) u[k] = ub[(size_t)k * tile_pts + e];
-#pragma unroll
-    for (int r = 0; r < SV; ++r) {
-      double2 acc = make_double2(0.0, 0.0);
-#pragma unroll
-      for (int c = 0; c < SV; ++c) {
-        const int lo = r < c ? r : c, hi = r < c ? c : r;
-        const int k = lo * SV - lo * (lo - 1) / 2 + (hi - lo);
-        if (c == 0) {
-          acc = cmul(u[k], x[c], dk);
-        } else {
-          acc.x = fma(u[k].x, x[c].x, acc.x);
-          acc.x = fma(-u[k].y, x[c].y, acc.x);
-          acc.y = fma(u[k].x, x[c].y, acc.y);
-          acc.y = fma(u[k].y, x[c].x, acc.y);
-        }
-      }
-      y[r] = acc;
-    }
+    matvec_sym<SV>(u, x, y);
 #pragma unroll
     for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + e] = y[s];
   }
@@ -163,14 +145,13 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
   double2* tb = sm + 2 * tsize;
   const long long ntiles = (SV == a.S) ? a.lines / G : (long long)a.S * a.lines / G;
   const int nslots = SV * G * (L / 8);
-  const DPK dk{a.one, a.mz};
 
   // register twiddles for the second stage of 64-point lines
   double2 wreg[8];
   if constexpr (L == 64) {
     const int k = (tid % (L / 8)) & 7;
 #pragma unroll
-    for (int r = 1; r < 8; ++r) wreg[r] = __ldg(&a.tw[r * k]);
+    for (int r = 1; r < 8; ++r) wreg[r] = __ldg(&((const double2*)a.tw)[r * k]);
   }
 
   __shared__ long long s_first;
@@ -179,7 +160,7 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
   long long cur = s_first;
   if (cur < ntiles) {
     const PqTile t = pq_tile(cur, SV, a);
-    pq_issue<L>(buf0, a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr);
+    pq_issue<L>(buf0, (double2*)a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr);
   }
   cp_async_commit();
   int b = 0;
@@ -189,7 +170,7 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
     const long long nxt = s_next;
     if (nxt < ntiles) {
       const PqTile t = pq_tile(nxt, SV, a);
-      pq_issue<L>(buf0 + (b ^ 1) * tsize, a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr);
+      pq_issue<L>(buf0 + (b ^ 1) * tsize, (double2*)a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr);
     }
     cp_async_commit();
     cp_async_wait<1>();  // this thread's copies of the current tile landed
@@ -200,29 +181,29 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
     const bool vstep = (SV > 1) && (a.U1 != nullptr);
     // stream the current tile's table entries in behind the first FFT
     if (vstep) {
-      pq_issue<L>(tb, a.U1, NP, a.P, t, G, a.stride, tid, nthr);
+      pq_issue<L>(tb, (const double2*)a.U1, NP, a.P, t, G, a.stride, tid, nthr);
     } else if (a.flags & PASS_T) {
-      pq_issue<L>(tb, a.tau, 1, a.P, t, G, a.stride, tid, nthr);
+      pq_issue<L>(tb, (const double2*)a.tau, 1, a.P, t, G, a.stride, tid, nthr);
     }
     cp_async_commit();
 
-    if (a.flags & PASS_INV_FIRST) fft_lines_pq<L, true>(x, a.tw, wreg, nslots, tid, nthr, dk);
+    if (a.flags & PASS_INV_FIRST) fft_lines_pq<L, true>(x, (const double2*)a.tw, wreg, nslots, tid, nthr);
     if (vstep) {
       cp_async_wait<0>();
       __syncthreads();
       // table and psi buffers share the [g][n] order, so pq_potential walks
       // both with one flat index
-      pq_potential<SV>(x, tb, tile_pts, tid, nthr, dk);
+      pq_potential<SV>(x, tb, tile_pts, tid, nthr);
       __syncthreads();
       if (a.U2) {
-        apply_potential<L, SV>(x, a.U2, t.tg, G, a.stride, a.P, tid, nthr, dk);
+        apply_potential<L, SV>(x, (const double2*)a.U2, t.tg, G, a.stride, a.P, tid, nthr);
       }
       if (a.flags & PASS_T) {  // 1-D grids: the kinetic phase follows in this pass
-        pq_issue<L>(tb, a.tau, 1, a.P, t, G, a.stride, tid, nthr);
+        pq_issue<L>(tb, (const double2*)a.tau, 1, a.P, t, G, a.stride, tid, nthr);
         cp_async_commit();
       }
     }
-    if (a.flags & PASS_FWD) fft_lines_pq<L, false>(x, a.tw, wreg, nslots, tid, nthr, dk);
+    if (a.flags & PASS_FWD) fft_lines_pq<L, false>(x, (const double2*)a.tw, wreg, nslots, tid, nthr);
     if (a.flags & PASS_T) {
       cp_async_wait<0>();
       __syncthreads();
@@ -231,7 +212,7 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
         const double2 ph = tb[e];
         for (int s = 0; s < SV; ++s) {
           double2* p = &x[(size_t)s * tile_pts + e];
-          *p = cmul(*p, ph, dk);
+          *p = cmul(*p, ph);
         }
       }
       __syncthreads();
@@ -239,20 +220,20 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
 #pragma unroll 1
         for (int e = tid; e < tile_pts; e += nthr) {
           const int g = e / L, n = e - (e / L) * L;
-          double2 ph = __ldg(&a.tau2[t.tg.addr(g, n, L, a.stride)]);
-          ph = make_double2(dmul(ph.x, a.tau2_scale, dk), dmul(ph.y, a.tau2_scale, dk));
+          double2 ph = __ldg(&((const double2*)a.tau2)[t.tg.addr(g, n, L, a.stride)]);
+          ph = cscale(ph, a.tau2_scale);
           for (int s = 0; s < SV; ++s) {
             double2* p = &x[(size_t)s * tile_pts + e];
-            *p = cmul(*p, ph, dk);
+            *p = cmul(*p, ph);
           }
         }
         __syncthreads();
       }
-      fft_lines_pq<L, true>(x, a.tw, wreg, nslots, tid, nthr, dk);
+      fft_lines_pq<L, true>(x, (const double2*)a.tw, wreg, nslots, tid, nthr);
     }
     __syncthreads();
     for (int s = 0; s < SV; ++s) {
-      double2* dst = a.psi + (size_t)(t.surf0 + s) * a.P;
+      double2* dst = (double2*)a.psi + (size_t)(t.surf0 + s) * a.P;
 #pragma unroll 1
       for (int e = tid; e < tile_pts; e += nthr) {
         int g, n;

@@ -94,8 +94,9 @@ struct dso_ctx {
   long long P = 0;
   // model and state
   int S = 0;
-  double* V = nullptr;       // packed [S(S+1)/2][P]
-  double2* psi = nullptr;    // [S][P]
+  int prec = DSO_FP64;       // DSO_FP64: complex128 storage; DSO_FP32: complex64
+  double* V = nullptr;       // packed [S(S+1)/2][P], always FP64
+  void* psi = nullptr;       // [S][P] complex in the context's precision
   bool have_V = false, have_psi = false;
   // scheme
   int order = 2, scheme = DSO_TRIPLE_JUMP, elementary = DSO_VTV;
@@ -104,14 +105,14 @@ struct dso_ctx {
   // tables for one dt
   bool tables_valid = false;
   double tables_dt = 0.0;
-  double2* Utab = nullptr;   // [na][S(S+1)/2][P]
-  double2* tau = nullptr;    // [nb][P]
+  void* Utab = nullptr;      // [na][S(S+1)/2][P] complex, context precision
+  void* tau = nullptr;       // [nb][P] complex, context precision
   double* tau_a = nullptr;   // [na] potential coefficient * dt
   int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
-  double2* tw[13] = {};      // per log2 L
+  void* tw[13] = {};         // per log2 L, context precision
   // observables
   double* Tax = nullptr;     // per-axis p^2 / (2 m_d), concatenated
-  double2* work = nullptr;   // [S][P]
+  void* work = nullptr;      // [S][P] complex, context precision
   double* partials = nullptr;
   double* obs_out = nullptr;
   // graph of one middle time step
@@ -124,9 +125,12 @@ struct dso_ctx {
   int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
   int64_t launches = 0;
+  size_t esz() const { return prec == DSO_FP32 ? 8 : 16; }  // bytes per complex element
 };
 
 namespace {
+
+void* at(void* base, size_t elems, size_t esz) { return base ? (char*)base + elems * esz : nullptr; }
 
 int ilog2(int64_t v) {
   int l = 0;
@@ -210,12 +214,14 @@ bool encode_view(CUtensorMap* m, const void* base, long long P, int L, long long
 cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   const int L = (int)c->n[p.axis];
   PassArgs a;
+  const size_t es = c->esz();
   a.psi = c->psi;
   const int NP = c->S * (c->S + 1) / 2;
-  a.U1 = p.u1 >= 0 ? c->Utab + (size_t)p.u1 * NP * c->P : nullptr;
-  a.U2 = p.u2 >= 0 ? c->Utab + (size_t)p.u2 * NP * c->P : nullptr;
-  a.tau = p.tb >= 0 ? c->tau + (size_t)p.tb * c->P : nullptr;
-  a.tau2 = p.tb2 >= 0 ? c->tau + (size_t)p.tb2 * c->P : nullptr;
+  a.U1 = p.u1 >= 0 ? at(c->Utab, (size_t)p.u1 * NP * c->P, es) : nullptr;
+  a.U2 = p.u2 >= 0 ? at(c->Utab, (size_t)p.u2 * NP * c->P, es) : nullptr;
+  a.tau = p.tb >= 0 ? at(c->tau, (size_t)p.tb * c->P, es) : nullptr;
+  a.tau2 = p.tb2 >= 0 ? at(c->tau, (size_t)p.tb2 * c->P, es) : nullptr;
+  a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
   a.tau2_scale = (double)c->P;
   a.tw = c->tw[ilog2(L)];
   a.P = c->P;
@@ -230,8 +236,6 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   if (a.G < 1 || (a.G & (a.G - 1)) || a.lines % a.G) return cudaErrorInvalidConfiguration;
   a.stride_log2 = ilog2(stride);
   a.G_log2 = ilog2(a.G);
-  a.one = 1.0;
-  a.mz = -0.0;
   a.ua = p.u1 >= 0 ? p.u1 : 0;
   a.ub = p.tb >= 0 ? p.tb : 0;
   a.err = c->err;
@@ -350,14 +354,22 @@ dso_status ensure_twiddles(dso_ctx* c) {
     const int l = ilog2(c->n[d]);
     if (c->tw[l]) continue;
     std::vector<double2> h = host_twiddles((int)c->n[d]);
-    CK(cudaMalloc(&c->tw[l], h.size() * sizeof(double2)));
-    CK(cudaMemcpy(c->tw[l], h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    if (c->prec == DSO_FP32) {
+      std::vector<float2> hf(h.size());
+      for (size_t i = 0; i < h.size(); ++i) hf[i] = make_float2((float)h[i].x, (float)h[i].y);
+      CK(cudaMalloc(&c->tw[l], hf.size() * sizeof(float2)));
+      CK(cudaMemcpy(c->tw[l], hf.data(), hf.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    } else {
+      CK(cudaMalloc(&c->tw[l], h.size() * sizeof(double2)));
+      CK(cudaMemcpy(c->tw[l], h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    }
   }
   return DSO_OK;
 }
 
 dso_status ensure_tables(dso_ctx* c, double dt) {
   if (c->tables_valid && c->tables_dt == dt) return DSO_OK;
+  CK(cudaGetLastError());  // surface any error left pending by an earlier call
   drop_tables(c);
   dso_status st = ensure_twiddles(c);
   if (st != DSO_OK) return st;
@@ -367,21 +379,22 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   const std::vector<double>& tco = (c->elementary == DSO_VTV) ? c->coeffs.b_unq : c->coeffs.a_unq;
   const int na = (int)vco.size(), nb = (int)tco.size();
   const int NP = c->S * (c->S + 1) / 2;
-  CK(cudaMalloc(&c->Utab, (size_t)na * NP * c->P * sizeof(double2)));
-  CK(cudaMalloc(&c->tau, (size_t)nb * c->P * sizeof(double2)));
+  CK(cudaMalloc(&c->Utab, (size_t)na * NP * c->P * c->esz()));
+  CK(cudaMalloc(&c->tau, (size_t)nb * c->P * c->esz()));
   CK(cudaMalloc(&c->tau_a, (size_t)na * sizeof(double)));
   c->n_vtab = na;
   c->n_ttab = nb;
   std::vector<double> ta(na);
   for (int u = 0; u < na; ++u) ta[u] = vco[u] * dt;
   CK(cudaMemcpyAsync(c->tau_a, ta.data(), na * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CK(launch_potential_tables(c->Utab, c->V, c->tau_a, na, c->S, c->P, c->stream));
+  CK(cudaGetLastError());
+  CK(launch_potential_tables(c->Utab, c->prec == DSO_FP32, c->V, c->tau_a, na, c->S, c->P, c->stream));
   c->launches += 1;
   std::vector<double2> fac = host_kinetic_factors(c->D, c->n, c->qmin, c->qmax, c->mass, tco, dt);
   double2* dfac = nullptr;
   CK(cudaMalloc(&dfac, fac.size() * sizeof(double2)));
   cudaError_t e = cudaMemcpyAsync(dfac, fac.data(), fac.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = launch_kinetic_tables(c->tau, dfac, nb, c->D, c->n, c->P, c->stream);
+  if (e == cudaSuccess) e = launch_kinetic_tables(c->tau, c->prec == DSO_FP32, dfac, nb, c->D, c->n, c->P, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(dfac);
   CK(e);
@@ -405,12 +418,12 @@ dso_status autotune_tiles(dso_ctx* c) {
     c->tuned = true;
     return DSO_OK;
   }
-  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * sizeof(double2)));
-  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * c->esz()));
+  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * c->esz(), cudaMemcpyDeviceToDevice, c->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   cudaError_t err = cudaEventCreate(&e1);
-  double2* keep = c->psi;
+  void* keep = c->psi;
   c->psi = c->work;
   const int64_t launches = c->launches;
   // every kind of pass (axis, surfaces staged) the propagation uses, with a
@@ -447,6 +460,7 @@ dso_status autotune_tiles(dso_ctx* c) {
         if (only >= 0 && var != only) continue;
         for (long long G = 1; G <= gmax && G <= lines && err == cudaSuccess; G *= 2) {
           if (any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
+          if (var != 0 && c->prec == DSO_FP32) continue;  // the other variants are FP64 only
           if (var == 1 && !axis_pass_pq_supported(L, SV, (int)G)) continue;
           if (var == 2 && !axis_pass_tma_supported(L, SV, (int)G)) continue;
           c->G[d][which] = (int)G;
@@ -528,7 +542,7 @@ extern "C" {
 dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_stream) {
   if (!out) return fail(DSO_EINVAL, "out is null");
   *out = nullptr;
-  if (precision != DSO_FP64) return fail(DSO_EINVAL, "only DSO_FP64 is part of this build");
+  if (precision != DSO_FP64 && precision != DSO_FP32) return fail(DSO_EINVAL, "precision must be DSO_FP64 or DSO_FP32");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(DSO_ECUDA, "no CUDA device");
   if (device < 0 || device >= ndev) return fail(DSO_EINVAL, "device index out of range");
@@ -537,6 +551,7 @@ dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_strea
   dso_ctx* c = new (std::nothrow) dso_ctx();
   if (!c) return fail(DSO_ENOMEM, "host allocation failed");
   c->device = device;
+  c->prec = precision;
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -621,7 +636,7 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   CK(cudaMalloc(&c->V, count * sizeof(double)));
   CK(cudaMemcpyAsync(c->V, V, count * sizeof(double), where == DSO_HOST ? cudaMemcpyHostToDevice
                                                                          : cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMalloc(&c->psi, (size_t)S * c->P * sizeof(double2)));
+  CK(cudaMalloc(&c->psi, (size_t)S * c->P * c->esz()));
   if (!c->queue) {
     CK(cudaMalloc(&c->queue, 2 * sizeof(unsigned)));
     CK(cudaMemsetAsync(c->queue, 0, 2 * sizeof(unsigned), c->stream));
@@ -667,11 +682,18 @@ dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {
   if (!c || !psi) return fail(DSO_EINVAL, "null argument");
   if (!c->have_V) return fail(DSO_ESTATE, "load the potential first (it fixes S)");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
-  const size_t bytes = (size_t)c->S * c->P * sizeof(double2);
+  const size_t bytes = (size_t)c->S * c->P * c->esz();
   if (where == DSO_HOST) {
-    const double* p = (const double*)psi;
-    for (size_t i = 0; i < 2 * (size_t)c->S * c->P; ++i)
-      if (!std::isfinite(p[i])) return fail(DSO_ENUMERIC, "psi has a non-finite value");
+    const size_t n = 2 * (size_t)c->S * c->P;
+    if (c->prec == DSO_FP32) {
+      const float* p = (const float*)psi;
+      for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return fail(DSO_ENUMERIC, "psi has a non-finite value");
+    } else {
+      const double* p = (const double*)psi;
+      for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return fail(DSO_ENUMERIC, "psi has a non-finite value");
+    }
   }
   DeviceGuard g(c->device);
   CK(cudaMemcpyAsync(c->psi, psi, bytes, where == DSO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
@@ -748,7 +770,7 @@ dso_status dso_get_psi(dso_ctx* c, void* out, int where) {
     dso_status fs = check_device_flag(c);
     if (fs != DSO_OK) return fs;
   }
-  const size_t bytes = (size_t)c->S * c->P * sizeof(double2);
+  const size_t bytes = (size_t)c->S * c->P * c->esz();
   CK(cudaMemcpyAsync(out, c->psi, bytes, where == DSO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                      c->stream));
   if (where == DSO_HOST) CK(cudaStreamSynchronize(c->stream));
@@ -773,12 +795,12 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
     CK(cudaMalloc(&c->Tax, h.size() * sizeof(double)));
     CK(cudaMemcpy(c->Tax, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
-  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * sizeof(double2)));
+  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * c->esz()));
   if (!c->partials) CK(cudaMalloc(&c->partials, (size_t)obs_partial_blocks() * DSO_OBS_COLS * sizeof(double)));
   if (!c->obs_out) CK(cudaMalloc(&c->obs_out, DSO_OBS_COLS * sizeof(double)));
   // momentum representation of a copy: forward FFT along every axis
-  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  double2* keep = c->psi;
+  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * c->esz(), cudaMemcpyDeviceToDevice, c->stream));
+  void* keep = c->psi;
   c->psi = c->work;
   cudaError_t e = cudaSuccess;
   for (int d = 0; d < c->D && e == cudaSuccess; ++d) e = run_pass(c, mkpass(d, 1, PASS_FWD));
@@ -787,6 +809,7 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
   ObsArgs a;
   a.psi = c->psi;
   a.psik = c->work;
+  a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
   a.V = c->V;
   a.Tax = c->Tax;
   for (int d = 0; d < 3; ++d) a.n[d] = c->n[d];

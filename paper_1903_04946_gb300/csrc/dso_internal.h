@@ -58,22 +58,25 @@ std::vector<double2> host_twiddles(int L);
 std::vector<double2> host_kinetic_factors(int D, const int64_t* n, const double* qmin, const double* qmax,
                                           const double* mass, const std::vector<double>& b_unq, double dt);
 // tau[u][g] = prod_d factor_d(u, k_d(g)) on the device.
-cudaError_t launch_kinetic_tables(double2* tau, const double2* factors, int nb, int D, const int64_t* n,
+// Output is double2, or float2 rounded from the FP64 product when fp32.
+cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double2* factors, int nb, int D, const int64_t* n,
                                   long long P, cudaStream_t st);
 // U[u][k][g] = exp(-i a_u dt V(q_g)) packed upper, for every unique a.
-cudaError_t launch_potential_tables(double2* U, const double* V, const double* tau_a, int na, int S,
+// FP64 throughout; stored as double2, or rounded once to float2 when fp32.
+cudaError_t launch_potential_tables(void* U, bool fp32, const double* V, const double* tau_a, int na, int S,
                                     long long P, cudaStream_t st);
 
 // Observables (observables.cu): per-block partial sums then a fixed-order
 // final reduction.  `spec` holds |psi~|^2-weighting per axis (p^2 / 2m).
 struct ObsArgs {
-  const double2* psi;     // position representation [S][P]
-  const double2* psik;    // momentum representation [S][P] (unnormalised FFT)
+  const void* psi;        // position representation [S][P] (double2, or float2 when fp32)
+  const void* psik;       // momentum representation [S][P] (unnormalised FFT)
   const double* V;        // packed potential [S(S+1)/2][P]
   const double* Tax;      // concatenated per-axis p_k^2/(2 m_d)
   int64_t n[3];
   int D, S;
   long long P;
+  int fp32;
 };
 int obs_partial_blocks();
 cudaError_t launch_observables(const ObsArgs& a, double* partials, double* out, cudaStream_t st);

@@ -24,6 +24,14 @@ constexpr int kMaxCols = DSO_OBS_COLS;
 
 int obs_partial_blocks() { return kBlocks; }
 
+__device__ __forceinline__ double2 load_c(const void* base, size_t i, int fp32) {
+  if (fp32) {
+    const float2 v = ((const float2*)base)[i];
+    return make_double2((double)v.x, (double)v.y);
+  }
+  return ((const double2*)base)[i];
+}
+
 __global__ void obs_partial_kernel(ObsArgs a, double* __restrict__ partials) {
   __shared__ double red[kThreads];
   const int ncol = a.S + 2;  // pops[S], <V>, <T> (unscaled)
@@ -33,7 +41,7 @@ __global__ void obs_partial_kernel(ObsArgs a, double* __restrict__ partials) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < a.P; g += stride) {
     double2 x[4];
     for (int s = 0; s < a.S; ++s) {
-      x[s] = a.psi[(size_t)s * a.P + g];
+      x[s] = load_c(a.psi, (size_t)s * a.P + g, a.fp32);
       acc[s] += x[s].x * x[s].x + x[s].y * x[s].y;
     }
     double ev = 0.0;
@@ -62,7 +70,7 @@ __global__ void obs_partial_kernel(ObsArgs a, double* __restrict__ partials) {
     }
     double m2 = 0.0;
     for (int s = 0; s < a.S; ++s) {
-      const double2 y = a.psik[(size_t)s * a.P + g];
+      const double2 y = load_c(a.psik, (size_t)s * a.P + g, a.fp32);
       m2 += y.x * y.x + y.y * y.y;
     }
     acc[a.S + 1] += T * m2;

@@ -11,14 +11,15 @@ enum PassFlags : int {
   PASS_T = 4,          // kinetic phase then inverse FFT after the forward FFT
 };
 
+// Complex arrays are double2 (FP64 path) or float2 (FP32 storage mode).
 struct PassArgs {
-  double2* psi;            // [S][P] wavefunction (in/out)
-  const double2* U1;       // [S(S+1)/2][P] potential unitary, or null
-  const double2* U2;       // second potential unitary, or null
-  const double2* tau;      // [P] kinetic phase (1/P folded in), or null
-  const double2* tau2;     // second kinetic phase (TVT step boundary), or null;
+  void* psi;               // [S][P] wavefunction (in/out)
+  const void* U1;          // [S(S+1)/2][P] potential unitary, or null
+  const void* U2;          // second potential unitary, or null
+  const void* tau;         // [P] kinetic phase (1/P folded in), or null
+  const void* tau2;        // second kinetic phase (TVT step boundary), or null;
                            // its folded 1/P is undone by tau2_scale = P (exact)
-  const double2* tw;       // [L] exp(-2 pi i m / L), m = 0..L-1
+  const void* tw;          // [L] exp(-2 pi i m / L), m = 0..L-1
   long long P;             // grid points per surface
   long long stride;        // element stride of the axis (product of later axes)
   long long lines;         // lines per surface = P / L
@@ -27,12 +28,11 @@ struct PassArgs {
   int flags;
   int stride_log2;         // log2(stride); every stride is a power of two
   int G_log2;              // log2(G)
-  double one;              // 1.0 and -0.0, passed at run time so that adds and
-  double mz;               // multiplies can be issued as FMAs (axis_pass.cuh)
   int ua;                  // unique-coefficient index of U1 (TMA variant)
   int ub;                  // unique-coefficient index of tau (TMA variant)
   int* err;                // device flag set when a bounded wait gives up
   double tau2_scale;       // P: both kinetic tables carry 1/P, one inverse FFT runs
+  int fp32;                // 1: complex arrays are float2 (FP32 storage mode)
 };
 
 }  // namespace dso

@@ -8,22 +8,27 @@
 
 namespace dso {
 
-template <int L, int SV>
-cudaError_t launch_one(const PassArgs& a, long long ntiles, cudaStream_t st) {
+template <int L, int SV, typename C>
+cudaError_t launch_one_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
   static bool attr_set[64] = {};  // the attribute is set once per device
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const int threads = SV * a.G * (L / 8);
-  const size_t smem = (size_t)SV * a.G * L * sizeof(double2);
+  const size_t smem = (size_t)SV * a.G * L * sizeof(C);
   if (threads > MaxThreads<L, SV>::value) return cudaErrorInvalidConfiguration;
   if (!attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(axis_pass_kernel<L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(axis_pass_kernel<L, SV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  axis_pass_kernel<L, SV><<<(unsigned)ntiles, threads, smem, st>>>(a);
+  axis_pass_kernel<L, SV, C><<<(unsigned)ntiles, threads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int L, int SV>
+cudaError_t launch_one(const PassArgs& a, long long ntiles, cudaStream_t st) {
+  return a.fp32 ? launch_one_t<L, SV, float2>(a, ntiles, st) : launch_one_t<L, SV, double2>(a, ntiles, st);
 }
 
 // Shared memory of the persistent variant: two psi tile buffers and one
@@ -81,6 +86,7 @@ cudaError_t launch_tma(const PassArgs& a, const TmaMaps* maps, long long ntiles,
 template <int L, int SV>
 cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, unsigned* queue, const TmaMaps* maps,
                            cudaStream_t st) {
+  if (variant != 0 && a.fp32) return cudaErrorInvalidConfiguration;  // FP64 only
   if (variant == 1) {
     if constexpr (SV * L / 8 <= 256) return launch_pq<L, SV>(a, ntiles, queue, st);
     return cudaErrorInvalidConfiguration;

@@ -56,7 +56,11 @@ std::vector<double2> host_kinetic_factors(int D, const int64_t* n, const double*
   return out;
 }
 
-__global__ void kinetic_table_kernel(double2* __restrict__ tau, const double2* __restrict__ fac, int nb, int D,
+__device__ __forceinline__ void store_c(double2* p, double x, double y) { *p = make_double2(x, y); }
+__device__ __forceinline__ void store_c(float2* p, double x, double y) { *p = make_float2((float)x, (float)y); }
+
+template <typename OutC>
+__global__ void kinetic_table_kernel(OutC* __restrict__ tau, const double2* __restrict__ fac, int nb, int D,
                                      int64_t n0, int64_t n1, int64_t n2, long long P) {
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= P) return;
@@ -77,13 +81,18 @@ __global__ void kinetic_table_kernel(double2* __restrict__ tau, const double2* _
     t = make_double2(t.x * x.x - t.y * x.y, t.x * x.y + t.y * x.x);
     off += nn[d];
   }
-  tau[(size_t)u * P + g] = t;
+  store_c(&tau[(size_t)u * P + g], t.x, t.y);
 }
 
-cudaError_t launch_kinetic_tables(double2* tau, const double2* factors, int nb, int D, const int64_t* n, long long P,
-                                  cudaStream_t st) {
+cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double2* factors, int nb, int D, const int64_t* n,
+                                  long long P, cudaStream_t st) {
   dim3 grid((unsigned)((P + 255) / 256), (unsigned)nb);
-  kinetic_table_kernel<<<grid, 256, 0, st>>>(tau, factors, nb, D, n[0], D > 1 ? n[1] : 1, D > 2 ? n[2] : 1, P);
+  if (fp32)
+    kinetic_table_kernel<<<grid, 256, 0, st>>>((float2*)tau, factors, nb, D, n[0], D > 1 ? n[1] : 1,
+                                               D > 2 ? n[2] : 1, P);
+  else
+    kinetic_table_kernel<<<grid, 256, 0, st>>>((double2*)tau, factors, nb, D, n[0], D > 1 ? n[1] : 1,
+                                               D > 2 ? n[2] : 1, P);
   return cudaGetLastError();
 }
 
@@ -134,8 +143,8 @@ __device__ void jacobi_eig(double (&A)[S][S], double (&W)[S][S], double (&lam)[S
   for (int i = 0; i < S; ++i) lam[i] = A[i][i];
 }
 
-template <int S>
-__global__ void potential_table_kernel(double2* __restrict__ U, const double* __restrict__ V,
+template <int S, typename OutC>
+__global__ void potential_table_kernel(OutC* __restrict__ U, const double* __restrict__ V,
                                        const double* __restrict__ tau_a, int na, long long P) {
   constexpr int NP = S * (S + 1) / 2;
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -154,10 +163,10 @@ __global__ void potential_table_kernel(double2* __restrict__ U, const double* __
       const double2 d0 = make_double2(cr, -s_over_r * vz);  // c - i s vz
       const double2 d1 = make_double2(cr, s_over_r * vz);   // c + i s vz
       const double2 od = make_double2(0.0, -s_over_r * vx); // -i s vx
-      double2* out = U + (size_t)u * NP * P;
-      out[g] = make_double2(cg * d0.x - sg * d0.y, cg * d0.y + sg * d0.x);
-      out[P + g] = make_double2(cg * od.x - sg * od.y, cg * od.y + sg * od.x);
-      out[2 * P + g] = make_double2(cg * d1.x - sg * d1.y, cg * d1.y + sg * d1.x);
+      OutC* out = U + (size_t)u * NP * P;
+      store_c(&out[g], cg * d0.x - sg * d0.y, cg * d0.y + sg * d0.x);
+      store_c(&out[P + g], cg * od.x - sg * od.y, cg * od.y + sg * od.x);
+      store_c(&out[2 * P + g], cg * d1.x - sg * d1.y, cg * d1.y + sg * d1.x);
     }
   } else {
     double A[S][S], W[S][S], lam[S];
@@ -174,7 +183,7 @@ __global__ void potential_table_kernel(double2* __restrict__ U, const double* __
       const double t = tau_a[u];
       double ph_re[S], ph_im[S];
       for (int m = 0; m < S; ++m) sincos(-t * lam[m], &ph_im[m], &ph_re[m]);
-      double2* out = U + (size_t)u * NP * P;
+      OutC* out = U + (size_t)u * NP * P;
       int kk = 0;
       for (int r = 0; r < S; ++r)
         for (int c = r; c < S; ++c) {
@@ -184,17 +193,16 @@ __global__ void potential_table_kernel(double2* __restrict__ U, const double* __
             re += w * ph_re[m];
             im += w * ph_im[m];
           }
-          out[(size_t)kk * P + g] = make_double2(re, im);
+          store_c(&out[(size_t)kk * P + g], re, im);
           ++kk;
         }
     }
   }
 }
 
-}  // namespace
-
-cudaError_t launch_potential_tables(double2* U, const double* V, const double* tau_a, int na, int S, long long P,
-                                    cudaStream_t st) {
+template <typename OutC>
+cudaError_t launch_potential_tables_t(OutC* U, const double* V, const double* tau_a, int na, int S, long long P,
+                                      cudaStream_t st) {
   const unsigned blocks = (unsigned)((P + 127) / 128);
   switch (S) {
     case 2: potential_table_kernel<2><<<blocks, 128, 0, st>>>(U, V, tau_a, na, P); break;
@@ -203,6 +211,14 @@ cudaError_t launch_potential_tables(double2* U, const double* V, const double* t
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_potential_tables(void* U, bool fp32, const double* V, const double* tau_a, int na, int S,
+                                    long long P, cudaStream_t st) {
+  return fp32 ? launch_potential_tables_t((float2*)U, V, tau_a, na, S, P, st)
+              : launch_potential_tables_t((double2*)U, V, tau_a, na, S, P, st);
 }
 
 }  // namespace dso

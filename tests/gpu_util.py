@@ -15,14 +15,15 @@ def require_gpu():
     return dso
 
 
-def gpu_propagate(problem, order, scheme, t, dt, psi=None, elementary="VTV"):
+def gpu_propagate(problem, order, scheme, t, dt, psi=None, elementary="VTV", fp32=False):
     import paper_1903_04946_gb300 as dso
     sch = dso.DSO_SUZUKI if scheme == "suzuki" else dso.DSO_TRIPLE_JUMP
     el = dso.DSO_TVT if elementary == "TVT" else dso.DSO_VTV
-    ctx = dso.Context(problem, order=order, scheme=sch, elementary=el)
+    ctx = dso.Context(problem, order=order, scheme=sch, elementary=el,
+                      precision=dso.DSO_FP32 if fp32 else dso.DSO_FP64)
     try:
         if psi is not None:
-            dso.dso_set_psi(ctx.ctx, psi)
+            ctx.set_psi(psi)
         ctx.propagate(t, dt)
         return ctx.psi()
     finally:
