@@ -28,13 +28,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "grid-pts x substeps/s"
 UNIT = "grid-pts*substeps/s"
-N_GRID = (64, 64, 64)
-S = 3
-ORDER, SCHEME_NAME = 6, "suzuki"
 T_FINAL = 2000.0
-DT = T_FINAL / 128          # 15.625 a.u.
 SEED = 1904
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+# Workloads.  The default is the 64^3 three-surface FP64 propagation the
+# metric is quoted on; "precision128" is the FP32 storage-and-FFT mode on a
+# 128^3 three-surface grid (orders 4 or 8), reported with its error against
+# the FP64 path.
+WORKLOADS = {
+    "pyrazine64": dict(grid=(64, 64, 64), S=3, order=6, scheme="suzuki", dt=T_FINAL / 128, fp32=False),
+    "precision128": dict(grid=(128, 128, 128), S=3, order=4, scheme="triple_jump", dt=T_FINAL / 128, fp32=True),
+}
+W = dict(WORKLOADS["pyrazine64"])
+N_GRID, S, ORDER, SCHEME_NAME, DT = W["grid"], W["S"], W["order"], W["scheme"], W["dt"]
+
+
+def select_workload(name, order=None):
+    global W, N_GRID, S, ORDER, SCHEME_NAME, DT
+    W = dict(WORKLOADS[name])
+    if order:
+        W["order"] = order
+    W["name"] = name
+    N_GRID, S, ORDER, SCHEME_NAME, DT = W["grid"], W["S"], W["order"], W["scheme"], W["dt"]
 
 
 def workload(seed=SEED):
@@ -42,16 +58,23 @@ def workload(seed=SEED):
     return synth.pyrazine_like(seed=seed, n=N_GRID, S=S)
 
 
+def scheme_code():
+    from paper_1903_04946_gb300 import DSO_SUZUKI, DSO_TRIPLE_JUMP
+    return DSO_SUZUKI if SCHEME_NAME == "suzuki" else DSO_TRIPLE_JUMP
+
+
 def substeps_per_step():
-    from paper_1903_04946_gb300 import DSO_SUZUKI, dso_scheme_coefficients
-    a, b, *_ = dso_scheme_coefficients(ORDER, DSO_SUZUKI)
+    from paper_1903_04946_gb300 import dso_scheme_coefficients
+    a, b, *_ = dso_scheme_coefficients(ORDER, scheme_code())
     return len(b)
 
 
 def config_dict(extra=None):
+    sname = "Suzuki" if SCHEME_NAME == "suzuki" else "triple-jump"
     d = {"workload": f"pyrazine-like 3-D vibronic model, {S} surfaces, "
-                     f"{'x'.join(map(str, N_GRID))} grid per surface, complex128, "
-                     f"Suzuki order {ORDER} (25 substeps/step), dt = {DT} a.u.",
+                     f"{'x'.join(map(str, N_GRID))} grid per surface, "
+                     f"{'complex64 storage and FFT' if W['fp32'] else 'complex128'}, "
+                     f"{sname} order {ORDER}, dt = {DT} a.u.",
          "grid": list(N_GRID), "surfaces": S, "order": ORDER, "scheme": SCHEME_NAME, "dt": DT,
          "seed": SEED, "parallelism": "independent wavepacket per GPU"}
     if extra:
@@ -152,7 +175,7 @@ def fp64_peak_tflops():
     return 152 * 2 * 2 * 2070e6 / 1e12
 
 
-def pass_flops_bytes(kind, n, S):
+def pass_flops_bytes(kind, n, S, esz=16):
     """Nominal algorithmic FLOPs and bytes of one launch of a pass kind:
     5 L log2 L flops per complex FFT of a length-L line, 8 S^2 - 2 S flops per
     grid point per S x S complex matvec, 6 flops per amplitude for the kinetic
@@ -169,10 +192,10 @@ def pass_flops_bytes(kind, n, S):
     flops = nfft * (amps // L) * 5 * L * math.log2(L)
     nU = (1 if f & 256 else 0) + (1 if f & 512 else 0)
     flops += nU * (8 * S * S - 2 * S) * P
-    bytes_ = 2 * 16 * amps + nU * 16 * (S * (S + 1) // 2) * P
+    bytes_ = 2 * esz * amps + nU * esz * (S * (S + 1) // 2) * P
     if f & 4:
         flops += 6 * amps
-        bytes_ += 16 * P
+        bytes_ += esz * P
     return flops, bytes_
 
 
@@ -187,8 +210,9 @@ def kind_name(k):
         parts.append(f"F{k['axis']}")
     if f & 4:
         parts.append(f"T I{k['axis']}")
-    name = "axis_pass_pq_kernel" if k.get("variant") == 1 else "axis_pass_kernel"
-    return "%s<L=%d,SV=%d> [%s]" % (name, N_GRID[k["axis"]], k["surfaces"], " ".join(parts))
+    name = {1: "axis_pass_pq_kernel", 2: "axis_pass_tma_kernel"}.get(k.get("variant"), "axis_pass_kernel")
+    return "%s<L=%d,SV=%d%s> [%s]" % (name, N_GRID[k["axis"]], k["surfaces"], ",float2" if W["fp32"] else "",
+                                      " ".join(parts))
 
 
 # --------------------------------------------------------------------------
@@ -213,10 +237,12 @@ def run_gpu(args):
     pr = workload(rank_seed(rank))
     nsub = substeps_per_step()
     pts = int(np.prod(N_GRID))
+    fp32 = W["fp32"]
+    esz = 8 if fp32 else 16
     stream = torch.cuda.Stream(device=device)
-    ctx = dso.Context(device=device, stream=stream)
+    ctx = dso.Context(device=device, stream=stream, precision=dso.DSO_FP32 if fp32 else dso.DSO_FP64)
     ctx.load_problem(pr)
-    dso.dso_set_scheme(ctx.ctx, ORDER, dso.DSO_SUZUKI)
+    dso.dso_set_scheme(ctx.ctx, ORDER, scheme_code())
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
 
     def barrier():
@@ -253,7 +279,7 @@ def run_gpu(args):
 
     # end to end through the public API with host buffers: each step copies
     # psi in from pinned host memory, propagates one step and reads psi back
-    host_in = torch.from_numpy(pr.psi0.copy()).pin_memory()
+    host_in = torch.from_numpy(pr.psi0.astype(np.complex64 if fp32 else np.complex128)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_steps = max(3, min(args.steps, 20))
     torch.cuda.synchronize()
@@ -267,7 +293,7 @@ def run_gpu(args):
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world, f"cuda:{device}")
-    bytes_psi = S * pts * 16
+    bytes_psi = S * pts * esz
     e2e = {"value": job_throughput(world, pts, nsub, e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": bytes_psi, "d2h_bytes_per_step": bytes_psi}
 
@@ -275,28 +301,54 @@ def run_gpu(args):
     # same pass list as the timed steps)
     kinds = dso.dso_profile_steps(ctx.ctx, DT, max(2, min(args.steps, 10)))
     for k in kinds:
-        k["flops"], k["bytes"] = pass_flops_bytes(k, N_GRID, S)
+        k["flops"], k["bytes"] = pass_flops_bytes(k, N_GRID, S, esz)
         k["ms_per_step"] = k["avg_ms"] * k["launches_per_step"]
     dom = max(kinds, key=lambda k: k["ms_per_step"])
-    peak = fp64_peak_tflops()
-    achieved = dom["flops"] / (dom["avg_ms"] * 1e-3) / 1e12
     prof_step_ms = sum(k["ms_per_step"] for k in kinds)
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        hbm_peak, hbm_src = 6800.0, "fallback"
+    if fp32:
+        achieved = dom["bytes"] / (dom["avg_ms"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(achieved / hbm_peak, 4), "traffic": None, "peak_source": hbm_src}
+    else:
+        peak = fp64_peak_tflops()
+        achieved = dom["flops"] / (dom["avg_ms"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": "FP64 unit count x max SM clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
+    roofline.update({
                 "kernel": kind_name(dom), "kernel_avg_us": round(dom["avg_ms"] * 1e3, 2),
                 "kernel_share_of_step": round(dom["ms_per_step"] / prof_step_ms, 4),
-                "peak_source": "FP64 unit count x max SM clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)",
                 "hbm_gbs_achieved": round(dom["bytes"] / (dom["avg_ms"] * 1e-3) / 1e9, 1),
                 "kinds": [{"kernel": kind_name(k), "avg_us": round(k["avg_ms"] * 1e3, 2),
                            "launches_per_step": k["launches_per_step"], "tile_lines": k["tile_lines"],
-                           "variant": ["tile", "persistent"][k["variant"]],
+                           "variant": ["tile", "persistent", "tma"][k["variant"]],
                            "tflops": round(k["flops"] / (k["avg_ms"] * 1e-3) / 1e12, 4),
-                           "gbs": round(k["bytes"] / (k["avg_ms"] * 1e-3) / 1e9, 1)} for k in kinds]}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        roofline["hbm_peak_gbs_measured"] = peaks.get("hbm_gbs")
-    except (OSError, ValueError):
-        pass
+                           "gbs": round(k["bytes"] / (k["avg_ms"] * 1e-3) / 1e9, 1)} for k in kinds]})
+    roofline["hbm_peak_gbs_measured"] = hbm_peak
+
+    precision = None
+    if fp32:
+        # error of the FP32 state against the FP64 path on the same input and
+        # the same number of steps (the FP64 GPU path stands in for the CPU
+        # oracle at this size; the tests pin it to the oracle)
+        nchk = max(2, min(args.steps, 8))
+        c32 = dso.Context(pr, device=device, order=ORDER, scheme=scheme_code(), precision=dso.DSO_FP32)
+        c64 = dso.Context(pr, device=device, order=ORDER, scheme=scheme_code(), precision=dso.DSO_FP64)
+        c32.propagate(nchk * DT, DT)
+        c64.propagate(nchk * DT, DT)
+        a32 = c32.psi().astype(np.complex128)
+        a64 = c64.psi()
+        n32, _, _ = c32.observables()
+        c32.close()
+        c64.close()
+        precision = {"steps": nchk, "rel_l2_vs_fp64": float(np.sqrt(np.sum(np.abs(a32 - a64) ** 2) /
+                                                                       np.sum(np.abs(a64) ** 2))),
+                     "norm_drift": float(abs(n32 - 1.0)), "reference": "FP64 GPU path, same input and steps"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -306,13 +358,16 @@ def run_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+                "data": "synthetic (seeded)",
                 "config": config_dict({"l2": "flushed before every timed step (256 MiB write outside the "
                                              "per-step CUDA events)",
                                        "substeps_per_step": nsub, "grid_points": pts}),
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk}
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if precision is not None:
+            line["precision"] = precision
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -352,7 +407,7 @@ def cpu_baseline(sample_substeps=20):
     dt = time.perf_counter() - t0
     return {"value": pts * sample_substeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{sample_substeps} substeps (potential action + FFT/phase/inverse FFT) of the same "
-                      f"64^3 x 3 workload, numpy FP64 oracle, single thread"}
+                      f"{'x'.join(map(str, N_GRID))} x {S} workload, numpy FP64 oracle, single thread"}
 
 
 def run_reference(args):
@@ -386,7 +441,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-substeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
+    ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
     args = ap.parse_args()
+    select_workload(args.workload, args.order or None)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
