@@ -89,6 +89,14 @@ void dso_destroy(dso_ctx* ctx);
 dso_status dso_set_grid(dso_ctx* ctx, int D, const int64_t* n, const double* qmin,
                         const double* qmax);
 
+/* Batch of B independent jobs (1..2^20) on the same grid, with the same
+ * masses and composition scheme but their own potentials and wavefunctions:
+ * the potential becomes [B][S(S+1)/2][grid] and psi [B][S][grid], and every
+ * pass of dso_propagate advances all B jobs (one launch per pass for the
+ * whole batch).  Call after dso_set_grid (which resets the batch to 1) and
+ * before dso_load_potential; resets potential, state and tables. */
+dso_status dso_set_batch(dso_ctx* ctx, int B);
+
 /* Diagonal mass matrix m of Eq. (diab_mol_ham): D positive values (host). */
 dso_status dso_set_masses(dso_ctx* ctx, const double* m);
 
@@ -123,9 +131,9 @@ dso_status dso_get_psi(dso_ctx* ctx, void* out, int where);
 
 /* Observables of Sec. II A on the current psi, in FP64: norm = ||psi||,
  * energy = <psi|H|psi> (kinetic part in the momentum representation,
- * potential part in the position representation), pops[s] = ||psi_s||^2
- * (host array of S entries).  Any output pointer may be NULL.  Synchronises
- * the stream. */
+ * potential part in the position representation), pops[s] = ||psi_s||^2.
+ * Host arrays with one entry per job (norm, energy: B entries; pops: B*S,
+ * job-major).  Any output pointer may be NULL.  Synchronises the stream. */
 dso_status dso_observables(dso_ctx* ctx, double* norm, double* energy, double* pops);
 
 /* Pruned splitting coefficients of a composed scheme (Sec. II D-F), host

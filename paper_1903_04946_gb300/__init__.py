@@ -23,7 +23,7 @@ DSO_TRIPLE_JUMP, DSO_SUZUKI = 0, 1
 DSO_VTV, DSO_TVT = 0, 1
 
 EXPORTS = (
-    "dso_create", "dso_destroy", "dso_set_grid", "dso_set_masses", "dso_load_potential",
+    "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
     "dso_position_observables_noalloc",
@@ -54,6 +54,7 @@ def load(path: str = LIB):
         "dso_destroy": (None, [vp]),
         "dso_set_grid": (i32, [vp, i32, ctypes.POINTER(i64), pd, pd]),
         "dso_set_masses": (i32, [vp, pd]),
+        "dso_set_batch": (i32, [vp, i32]),
         "dso_load_potential": (i32, [vp, i32, vp, i32]),
         "dso_set_scheme": (i32, [vp, i32, i32, i32, i32]),
         "dso_set_psi": (i32, [vp, vp, i32]),
@@ -125,6 +126,10 @@ def dso_set_grid(ctx, n, qmin, qmax):
                                (ctypes.c_double * D)(*[float(x) for x in qmax])), "dso_set_grid")
 
 
+def dso_set_batch(ctx, B):
+    _check(load().dso_set_batch(ctx, int(B)), "dso_set_batch")
+
+
 def dso_set_masses(ctx, m):
     D = len(m)
     _check(load().dso_set_masses(ctx, (ctypes.c_double * D)(*[float(x) for x in m])), "dso_set_masses")
@@ -162,11 +167,14 @@ def dso_get_psi(ctx, out):
     return out
 
 
-def dso_observables(ctx, S):
-    norm, energy = ctypes.c_double(), ctypes.c_double()
-    pops = (ctypes.c_double * S)()
-    _check(load().dso_observables(ctx, ctypes.byref(norm), ctypes.byref(energy), pops), "dso_observables")
-    return norm.value, energy.value, np.array(pops[:], dtype=np.float64)
+def dso_observables(ctx, S, B=1):
+    """(norm, energy, pops); with B > 1 jobs, arrays of B, B and (B, S)."""
+    norm, energy = (ctypes.c_double * B)(), (ctypes.c_double * B)()
+    pops = (ctypes.c_double * (B * S))()
+    _check(load().dso_observables(ctx, norm, energy, pops), "dso_observables")
+    if B == 1:
+        return norm[0], energy[0], np.array(pops[:], dtype=np.float64)
+    return (np.array(norm[:]), np.array(energy[:]), np.array(pops[:], dtype=np.float64).reshape(B, S))
 
 
 def dso_scheme_coefficients(order, scheme=DSO_TRIPLE_JUMP):
@@ -231,6 +239,7 @@ class Context:
         self.ctx = dso_create(device, precision, stream)
         self.dtype = np.complex64 if precision == DSO_FP32 else np.complex128
         self.S = None
+        self.B = 1
         self.shape = None
         if problem is not None:
             self.load_problem(problem)
@@ -242,7 +251,24 @@ class Context:
         dso_load_potential(self.ctx, pr.S, pr.V)
         dso_set_psi(self.ctx, np.ascontiguousarray(pr.psi0, dtype=self.dtype))
         self.S = pr.S
+        self.B = 1
         self.shape = (pr.S,) + tuple(pr.n)
+
+    def load_batch(self, problems):
+        """B jobs on one grid (same n, qmin, qmax, masses, S), each with its
+        own potential and initial state."""
+        p0 = problems[0]
+        for pr in problems[1:]:
+            if (pr.n, pr.qmin, pr.qmax, pr.mass, pr.S) != (p0.n, p0.qmin, p0.qmax, p0.mass, p0.S):
+                raise ValueError("batched jobs must share grid, masses and surface count")
+        dso_set_grid(self.ctx, p0.n, p0.qmin, p0.qmax)
+        dso_set_batch(self.ctx, len(problems))
+        dso_set_masses(self.ctx, p0.mass)
+        dso_load_potential(self.ctx, p0.S, np.ascontiguousarray(np.stack([pr.V for pr in problems])))
+        dso_set_psi(self.ctx, np.ascontiguousarray(np.stack([pr.psi0 for pr in problems]), dtype=self.dtype))
+        self.S = p0.S
+        self.B = len(problems)
+        self.shape = (self.B, p0.S) + tuple(p0.n)
 
     def propagate(self, t, dt):
         dso_propagate(self.ctx, t, dt)
@@ -255,7 +281,7 @@ class Context:
         return dso_get_psi(self.ctx, out)
 
     def observables(self):
-        return dso_observables(self.ctx, self.S)
+        return dso_observables(self.ctx, self.S, self.B)
 
     def close(self):
         if self.ctx is not None:

@@ -73,5 +73,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))
+    extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
+    if "--debug-bounds" in sys.argv:  # bounds-checked kernels (diagnostics)
+        extra.append("-DDSO_DEBUG_BOUNDS")
+    print(build(force="--force" in sys.argv or "--debug-bounds" in sys.argv, verbose="-v" in sys.argv,
+                extra=extra))

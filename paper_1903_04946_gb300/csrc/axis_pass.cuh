@@ -251,6 +251,21 @@ struct TileGeom {
   }
 };
 
+__device__ __forceinline__ TileJob split_tile(long long tile, int SV, const PassArgs& a) {
+  TileJob t;
+  const long long per_set = a.lines >> a.G_log2;  // tiles per line set (one surface, or one job's S)
+  const long long set = tile / per_set;
+  t.tile = tile - set * per_set;
+  if (SV == 1) {
+    t.surf0 = (int)set;
+    t.job = (int)(set / a.S);
+  } else {
+    t.job = (int)set;
+    t.surf0 = (int)set * a.S;
+  }
+  return t;
+}
+
 __device__ __forceinline__ TileGeom make_geom(long long tile, const PassArgs& a) {
   TileGeom tg;
   const long long lam0 = tile << a.G_log2;
@@ -296,9 +311,28 @@ __device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], cons
   }
 }
 
+// With DSO_DEBUG_BOUNDS every global access of the tile kernel is checked
+// against its allocation; a bad index sets *err and the access is skipped.
+#ifdef DSO_DEBUG_BOUNDS
+#define DSO_CHECK_INDEX(idx, extent, code, err) \
+  (((idx) >= 0 && (idx) < (extent)) ? true : (atomicExch((err), (code)), false))
+// first bad access of the tile kernel, with its tile context: err[1..15]
+#define DSO_RECORD(err, v0, v1, v2, v3, v4, v5, v6, v7)                    \
+  do {                                                                  \
+    if (atomicCAS((err) + 1, 0, 1) == 0) {                              \
+      (err)[2] = (int)(v0); (err)[3] = (int)(v1); (err)[4] = (int)(v2); \
+      (err)[5] = (int)(v3); (err)[6] = (int)(v4); (err)[7] = (int)(v5); \
+      (err)[8] = (int)(v6); (err)[9] = (int)(v7);                       \
+    }                                                                   \
+  } while (0)
+#else
+#define DSO_CHECK_INDEX(idx, extent, code, err) true
+#endif
+
 template <int L, int SV, typename C>
 __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, const TileGeom& tg, int G,
-                                                long long stride, long long P, int tid, int nthr) {
+                                                long long stride, long long P, int tid, int nthr,
+                                                const PassArgs* dbg = nullptr) {
   constexpr int NP = SV * (SV + 1) / 2;
   const int tile_pts = G * L;
   for (int e = tid; e < tile_pts; e += nthr) {
@@ -310,7 +344,18 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
 #pragma unroll
     for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + off];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) u[k] = __ldg(&U[(size_t)k * P + gi]);
+    for (int k = 0; k < NP; ++k) {
+#ifdef DSO_DEBUG_BOUNDS
+      if (dbg) {
+        const long long off = (long long)(&U[(size_t)k * P + gi] - (const C*)dbg->U_base);
+        if (!DSO_CHECK_INDEX(off, dbg->u_elems, 102, dbg->err)) {
+          u[k] = mkc((RealT<C>)0, (RealT<C>)0);
+          continue;
+        }
+      }
+#endif
+      u[k] = __ldg(&U[(size_t)k * P + gi]);
+    }
     matvec_sym<SV>(u, x, y);
 #pragma unroll
     for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + off] = y[s];
@@ -322,11 +367,18 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
 // one, whose 1/P factor belongs to an inverse FFT that does not run twice).
 template <int L, typename C>
 __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, const TileGeom& tg, int G, int SVl,
-                                              long long stride, int tid, int nthr, RealT<C> scale = 1) {
+                                              long long stride, int tid, int nthr, RealT<C> scale = 1,
+                                              const PassArgs* dbg = nullptr) {
   const int tile_pts = G * L;
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
+#ifdef DSO_DEBUG_BOUNDS
+    if (dbg) {
+      const long long off = (long long)(&tau[tg.addr(g, n, L, stride)] - (const C*)dbg->tau_base);
+      if (!DSO_CHECK_INDEX(off, dbg->tau_elems, 103, dbg->err)) continue;
+    }
+#endif
     C t = __ldg(&tau[tg.addr(g, n, L, stride)]);
     if (scale != (RealT<C>)1) t = cscale(t, scale);
     const int off = g * L + n;
@@ -356,15 +408,11 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int G = a.G;
   const int tile_pts = G * L;
-  const long long tiles_per_surface = a.lines / G;
-  long long tile = blockIdx.x;
-  int surf0 = 0;
-  if (SV == 1) {
-    surf0 = (int)(tile / tiles_per_surface);
-    tile = tile - (long long)surf0 * tiles_per_surface;
-  }
+  const TileJob tj = split_tile(blockIdx.x, SV, a);
+  const int surf0 = tj.surf0;
+  const size_t uoff = (size_t)tj.job * a.u_batch_stride;
   // line id lambda = o * stride + i; the tile covers lambdas [tile*G, tile*G+G)
-  const TileGeom tg = make_geom(tile, a);
+  const TileGeom tg = make_geom(tj.tile, a);
 
   // load
   for (int s = 0; s < SV; ++s) {
@@ -372,7 +420,9 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, tg, g, n);
-      sm[(size_t)s * tile_pts + g * L + n] = src[tg.addr(g, n, L, a.stride)];
+      const long long gidx = (long long)(surf0 + s) * a.P + tg.addr(g, n, L, a.stride);
+      if (DSO_CHECK_INDEX(gidx, a.psi_elems, 100, a.err))
+        sm[(size_t)s * tile_pts + g * L + n] = src[tg.addr(g, n, L, a.stride)];
     }
   }
   __syncthreads();
@@ -386,16 +436,18 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
     __syncthreads();
   }
   if (SV > 1) {  // the host sets U1/U2 only for passes that stage all S surfaces
-    if (a.U1) apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U1), tg, G, a.stride, a.P, tid, nthr);
-    if (a.U2) apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U2), tg, G, a.stride, a.P, tid, nthr);
+    if (a.U1)
+      apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U1) + uoff, tg, G, a.stride, a.P, tid, nthr, &a);
+    if (a.U2)
+      apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U2) + uoff, tg, G, a.stride, a.P, tid, nthr, &a);
   }
   if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, tw, nslots, tid, nthr);
   if (a.flags & PASS_T) {
     __syncthreads();
-    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr);
+    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr, (RealT<C>)1, &a);
     if (a.tau2)
       apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau2), tg, G, SV, a.stride, tid, nthr,
-                       (RealT<C>)a.tau2_scale);
+                       (RealT<C>)a.tau2_scale, &a);
     fft_lines<L, true, K>(sm, tw, nslots, tid, nthr);
   }
   __syncthreads();
@@ -406,7 +458,13 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, tg, g, n);
-      dst[tg.addr(g, n, L, a.stride)] = sm[(size_t)s * tile_pts + g * L + n];
+      const long long gidx = (long long)(surf0 + s) * a.P + tg.addr(g, n, L, a.stride);
+#ifdef DSO_DEBUG_BOUNDS
+      if (gidx < 0 || gidx >= a.psi_elems)
+        DSO_RECORD(a.err, blockIdx.x, surf0, tg.o0, tg.i0, g, n, a.G, (a.stride_log2 << 16) | (tg.Wi_log2 << 8) | s);
+#endif
+      if (DSO_CHECK_INDEX(gidx, a.psi_elems, 101, a.err))
+        dst[tg.addr(g, n, L, a.stride)] = sm[(size_t)s * tile_pts + g * L + n];
     }
   }
 }

@@ -81,17 +81,15 @@ __device__ __forceinline__ void fft_lines_pq(double2* sm, const double2* __restr
 struct PqTile {
   TileGeom tg;
   int surf0;
+  size_t uoff;  // this job's offset into the potential tables
 };
 
 __device__ __forceinline__ PqTile pq_tile(long long tile, int SV, const PassArgs& a) {
   PqTile t;
-  const long long tiles_per_surface = a.lines >> a.G_log2;
-  t.surf0 = 0;
-  if (SV == 1) {
-    t.surf0 = (int)(tile / tiles_per_surface);
-    tile = tile - (long long)t.surf0 * tiles_per_surface;
-  }
-  t.tg = make_geom(tile, a);
+  const TileJob tj = split_tile(tile, SV, a);
+  t.surf0 = tj.surf0;
+  t.uoff = (size_t)tj.job * a.u_batch_stride;
+  t.tg = make_geom(tj.tile, a);
   return t;
 }
 
@@ -99,7 +97,8 @@ __device__ __forceinline__ PqTile pq_tile(long long tile, int SV, const PassArgs
 // `src` ([count][P] layout, or [S][P] for psi) into `dst` ([count][G*L]).
 template <int L>
 __device__ __forceinline__ void pq_issue(double2* dst, const double2* src, int count, long long P, const PqTile& t,
-                                         int G, long long stride, int tid, int nthr) {
+                                         int G, long long stride, int tid, int nthr, const double2* base = nullptr,
+                                         long long extent = 0, int* err = nullptr) {
   const int tile_pts = G * L;
 #pragma unroll 1
   for (int c = 0; c < count; ++c) {
@@ -109,6 +108,9 @@ __device__ __forceinline__ void pq_issue(double2* dst, const double2* src, int c
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, t.tg, g, n);
+#ifdef DSO_DEBUG_BOUNDS
+      if (base && !DSO_CHECK_INDEX((long long)(&s[t.tg.addr(g, n, L, stride)] - base), extent, 110, err)) continue;
+#endif
       cp_async16(&d[g * L + n], &s[t.tg.addr(g, n, L, stride)]);
     }
   }
@@ -143,7 +145,8 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
   const int tsize = SV * tile_pts;
   double2* const buf0 = sm;
   double2* tb = sm + 2 * tsize;
-  const long long ntiles = (SV == a.S) ? a.lines / G : (long long)a.S * a.lines / G;
+  const long long ntiles = (SV == a.S) ? (long long)a.nbatch * (a.lines / G)
+                                       : (long long)a.nbatch * a.S * (a.lines / G);
   const int nslots = SV * G * (L / 8);
 
   // register twiddles for the second stage of 64-point lines
@@ -160,7 +163,8 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
   long long cur = s_first;
   if (cur < ntiles) {
     const PqTile t = pq_tile(cur, SV, a);
-    pq_issue<L>(buf0, (double2*)a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr);
+    pq_issue<L>(buf0, (double2*)a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr,
+                (const double2*)a.psi, a.psi_elems, a.err);
   }
   cp_async_commit();
   int b = 0;
@@ -170,7 +174,8 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
     const long long nxt = s_next;
     if (nxt < ntiles) {
       const PqTile t = pq_tile(nxt, SV, a);
-      pq_issue<L>(buf0 + (b ^ 1) * tsize, (double2*)a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid, nthr);
+      pq_issue<L>(buf0 + (b ^ 1) * tsize, (double2*)a.psi + (size_t)t.surf0 * a.P, SV, a.P, t, G, a.stride, tid,
+                  nthr, (const double2*)a.psi, a.psi_elems, a.err);
     }
     cp_async_commit();
     cp_async_wait<1>();  // this thread's copies of the current tile landed
@@ -181,9 +186,11 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
     const bool vstep = (SV > 1) && (a.U1 != nullptr);
     // stream the current tile's table entries in behind the first FFT
     if (vstep) {
-      pq_issue<L>(tb, (const double2*)a.U1, NP, a.P, t, G, a.stride, tid, nthr);
+      pq_issue<L>(tb, (const double2*)a.U1 + t.uoff, NP, a.P, t, G, a.stride, tid, nthr,
+                  (const double2*)a.U_base, a.u_elems, a.err);
     } else if (a.flags & PASS_T) {
-      pq_issue<L>(tb, (const double2*)a.tau, 1, a.P, t, G, a.stride, tid, nthr);
+      pq_issue<L>(tb, (const double2*)a.tau, 1, a.P, t, G, a.stride, tid, nthr, (const double2*)a.tau_base,
+                  a.tau_elems, a.err);
     }
     cp_async_commit();
 
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
       pq_potential<SV>(x, tb, tile_pts, tid, nthr);
       __syncthreads();
       if (a.U2) {
-        apply_potential<L, SV>(x, (const double2*)a.U2, t.tg, G, a.stride, a.P, tid, nthr);
+        apply_potential<L, SV>(x, (const double2*)a.U2 + t.uoff, t.tg, G, a.stride, a.P, tid, nthr);
       }
       if (a.flags & PASS_T) {  // 1-D grids: the kinetic phase follows in this pass
         pq_issue<L>(tb, (const double2*)a.tau, 1, a.P, t, G, a.stride, tid, nthr);
@@ -238,7 +245,8 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
       for (int e = tid; e < tile_pts; e += nthr) {
         int g, n;
         tile_elem<L>(e, t.tg, g, n);
-        dst[t.tg.addr(g, n, L, a.stride)] = x[(size_t)s * tile_pts + g * L + n];
+        if (DSO_CHECK_INDEX((long long)(t.surf0 + s) * a.P + t.tg.addr(g, n, L, a.stride), a.psi_elems, 111, a.err))
+          dst[t.tg.addr(g, n, L, a.stride)] = x[(size_t)s * tile_pts + g * L + n];
       }
     }
     cur = nxt;

@@ -222,14 +222,9 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
   volatile int* status = (volatile int*)(bar + 3);
 
   // tile geometry (the same as axis_pass_kernel)
-  long long tile = blockIdx.x;
-  int surf0 = 0;
-  if (SV == 1) {
-    const long long tps = a.lines >> a.G_log2;
-    surf0 = (int)(tile / tps);
-    tile -= (long long)surf0 * tps;
-  }
-  const TileGeom tg = make_geom(tile, a);
+  const TileJob tj = split_tile(blockIdx.x, SV, a);
+  const int surf0 = tj.surf0;
+  const TileGeom tg = make_geom(tj.tile, a);
   const int Wi_log2 = tg.Wi_log2;
   const int c1 = (int)tg.i0, c3 = (int)tg.o0;
   const bool vstep = (SV > 1) && (a.U1 != nullptr);
@@ -250,7 +245,9 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
     bulk_load(tws, a.tw, (unsigned)(L * sizeof(double2)), &bar[0]);
     if (vstep) {
       mbar_expect_tx(&bar[1], (unsigned)(NP * tile_pts * sizeof(double2)));
-      tma_load_5d(tb, &maps.tab, 0, c1, 0, c3, a.ua * NP, &bar[1]);
+      // potential tables are [job][unique a][component]: one coordinate
+      tma_load_5d(tb, &maps.tab, 0, c1, 0, c3, (int)((long long)tj.job * a.u_batch_stride / a.P) + a.ua * NP,
+                  &bar[1]);
     } else if (tstep) {
       mbar_expect_tx(&bar[1], (unsigned)(tile_pts * sizeof(double2)));
       tma_load_5d(tb, &maps.tab, 0, c1, 0, c3, a.ub, &bar[1]);
@@ -276,7 +273,8 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
     tma_potential<SV>(x, tb, tile_pts, tid, nthr);
     __syncthreads();
     if (a.U2) {
-      tma_potential_global<L, SV>(x, (const double2*)a.U2, a, tg.o0, tg.i0, Wi_log2, tile_pts, tid, nthr);
+      tma_potential_global<L, SV>(x, (const double2*)a.U2 + (size_t)tj.job * a.u_batch_stride, a, tg.o0, tg.i0,
+                                  Wi_log2, tile_pts, tid, nthr);
       __syncthreads();
     }
     if (tstep && tid == 0) {  // 1-D grids: kinetic phases into the freed table buffer

@@ -93,6 +93,7 @@ struct dso_ctx {
   bool have_grid = false, have_mass = false;
   long long P = 0;
   // model and state
+  int B = 1;                 // independent jobs sharing grid, masses and scheme
   int S = 0;
   int prec = DSO_FP64;       // DSO_FP64: complex128 storage; DSO_FP32: complex64
   double* V = nullptr;       // packed [S(S+1)/2][P], always FP64
@@ -213,7 +214,7 @@ bool encode_view(CUtensorMap* m, const void* base, long long P, int L, long long
 
 cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   const int L = (int)c->n[p.axis];
-  PassArgs a;
+  PassArgs a{};  // every field defined; the kernels read all of them
   const size_t es = c->esz();
   a.psi = c->psi;
   const int NP = c->S * (c->S + 1) / 2;
@@ -239,7 +240,15 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.ua = p.u1 >= 0 ? p.u1 : 0;
   a.ub = p.tb >= 0 ? p.tb : 0;
   a.err = c->err;
-  const long long ntiles = (p.SV == c->S) ? a.lines / a.G : (long long)c->S * a.lines / a.G;
+  a.nbatch = c->B;
+  a.u_batch_stride = (long long)c->n_vtab * NP * c->P;
+  a.U_base = c->Utab;
+  a.tau_base = c->tau;
+  a.psi_elems = (long long)c->B * c->S * c->P;
+  a.u_elems = (long long)c->B * c->n_vtab * NP * c->P;
+  a.tau_elems = (long long)c->n_ttab * c->P;
+  const long long ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G)
+                                          : (long long)c->B * c->S * (a.lines / a.G);
   const int variant = c->variant[p.axis][which];
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
@@ -247,13 +256,23 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
     const int Wi = (int)(stride < a.G ? stride : a.G);
     const int Go = a.G / Wi;
     const int NP = c->S * (c->S + 1) / 2;
-    bool ok = encode_view(&maps.psi, c->psi, c->P, L, stride, c->S, Wi, Go, p.SV);
+    bool ok = encode_view(&maps.psi, c->psi, c->P, L, stride, (long long)c->B * c->S, Wi, Go, p.SV);
     if (ok && p.u1 >= 0)
-      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)NP * (long long)c->n_vtab, Wi, Go, NP);
+      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)c->B * NP * (long long)c->n_vtab, Wi, Go,
+                       NP);
     if (ok && p.tb >= 0) {
       CUtensorMap* m = (p.u1 >= 0) ? &maps.tab2 : &maps.tab;
       ok = encode_view(m, c->tau, c->P, L, stride, (long long)c->n_ttab, Wi, Go, 1);
     }
+    // every box the kernel will address must lie inside its tensor
+    const long long outer = c->P / ((long long)L * stride);
+    const long long t_per_set = a.lines / a.G;
+    const long long i_last = ((t_per_set - 1) * a.G) % stride, o_last = ((t_per_set - 1) * a.G) / stride;
+    if (i_last + Wi > stride || o_last + Go > outer) ok = false;
+    if (p.u1 >= 0 && ((long long)(c->B - 1) * c->n_vtab * NP + (long long)p.u1 * NP + NP >
+                      (long long)c->B * c->n_vtab * NP))
+      ok = false;
+    if (p.tb >= 0 && p.tb >= c->n_ttab) ok = false;
     if (!ok) return cudaErrorInvalidConfiguration;
   }
   c->launches += 1;
@@ -379,7 +398,7 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   const std::vector<double>& tco = (c->elementary == DSO_VTV) ? c->coeffs.b_unq : c->coeffs.a_unq;
   const int na = (int)vco.size(), nb = (int)tco.size();
   const int NP = c->S * (c->S + 1) / 2;
-  CK(cudaMalloc(&c->Utab, (size_t)na * NP * c->P * c->esz()));
+  CK(cudaMalloc(&c->Utab, (size_t)c->B * na * NP * c->P * c->esz()));
   CK(cudaMalloc(&c->tau, (size_t)nb * c->P * c->esz()));
   CK(cudaMalloc(&c->tau_a, (size_t)na * sizeof(double)));
   c->n_vtab = na;
@@ -388,8 +407,11 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   for (int u = 0; u < na; ++u) ta[u] = vco[u] * dt;
   CK(cudaMemcpyAsync(c->tau_a, ta.data(), na * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaGetLastError());
-  CK(launch_potential_tables(c->Utab, c->prec == DSO_FP32, c->V, c->tau_a, na, c->S, c->P, c->stream));
-  c->launches += 1;
+  for (int b = 0; b < c->B; ++b) {
+    CK(launch_potential_tables(at(c->Utab, (size_t)b * na * NP * c->P, c->esz()), c->prec == DSO_FP32,
+                               c->V + (size_t)b * NP * c->P, c->tau_a, na, c->S, c->P, c->stream));
+    c->launches += 1;
+  }
   std::vector<double2> fac = host_kinetic_factors(c->D, c->n, c->qmin, c->qmax, c->mass, tco, dt);
   double2* dfac = nullptr;
   CK(cudaMalloc(&dfac, fac.size() * sizeof(double2)));
@@ -418,8 +440,9 @@ dso_status autotune_tiles(dso_ctx* c) {
     c->tuned = true;
     return DSO_OK;
   }
-  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * c->esz()));
-  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * c->esz(), cudaMemcpyDeviceToDevice, c->stream));
+  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->B * c->S * c->P * c->esz()));
+  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->B * c->S * c->P * c->esz(), cudaMemcpyDeviceToDevice,
+                     c->stream));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   cudaError_t err = cudaEventCreate(&e1);
@@ -599,6 +622,18 @@ dso_status dso_set_grid(dso_ctx* c, int D, const int64_t* n, const double* qmin,
   }
   c->have_grid = true;
   c->have_mass = false;
+  c->B = 1;
+  return DSO_OK;
+}
+
+dso_status dso_set_batch(dso_ctx* c, int B) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (!c->have_grid) return fail(DSO_ESTATE, "grid not set");
+  if (B < 1 || B > (1 << 20)) return fail(DSO_EINVAL, "batch must be 1..2^20");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_model(c);
+  c->B = B;
   return DSO_OK;
 }
 
@@ -624,7 +659,7 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   for (int d = 0; d < c->D; ++d)
     if (!axis_pass_supported((int)c->n[d], d == 0 ? S : 1) || (c->D == 1 && !axis_pass_supported((int)c->n[0], S)))
       return fail(DSO_EINVAL, "axis length too long for this surface count (S * n[0] must be <= 8192)");
-  const size_t count = (size_t)(S * (S + 1) / 2) * c->P;
+  const size_t count = (size_t)c->B * (S * (S + 1) / 2) * c->P;
   if (where == DSO_HOST) {
     for (size_t i = 0; i < count; ++i)
       if (!std::isfinite(V[i])) return fail(DSO_ENUMERIC, "potential has a non-finite value");
@@ -636,14 +671,14 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   CK(cudaMalloc(&c->V, count * sizeof(double)));
   CK(cudaMemcpyAsync(c->V, V, count * sizeof(double), where == DSO_HOST ? cudaMemcpyHostToDevice
                                                                          : cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMalloc(&c->psi, (size_t)S * c->P * c->esz()));
+  CK(cudaMalloc(&c->psi, (size_t)c->B * S * c->P * c->esz()));
   if (!c->queue) {
     CK(cudaMalloc(&c->queue, 2 * sizeof(unsigned)));
     CK(cudaMemsetAsync(c->queue, 0, 2 * sizeof(unsigned), c->stream));
   }
   if (!c->err) {
-    CK(cudaMalloc(&c->err, sizeof(int)));
-    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    CK(cudaMalloc(&c->err, 16 * sizeof(int)));
+    CK(cudaMemsetAsync(c->err, 0, 16 * sizeof(int), c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
   for (int d = 0; d < c->D; ++d) {
@@ -682,9 +717,9 @@ dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {
   if (!c || !psi) return fail(DSO_EINVAL, "null argument");
   if (!c->have_V) return fail(DSO_ESTATE, "load the potential first (it fixes S)");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
-  const size_t bytes = (size_t)c->S * c->P * c->esz();
+  const size_t bytes = (size_t)c->B * c->S * c->P * c->esz();
   if (where == DSO_HOST) {
-    const size_t n = 2 * (size_t)c->S * c->P;
+    const size_t n = 2 * (size_t)c->B * c->S * c->P;
     if (c->prec == DSO_FP32) {
       const float* p = (const float*)psi;
       for (size_t i = 0; i < n; ++i)
@@ -751,12 +786,17 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
 // the next synchronising call.
 static dso_status check_device_flag(dso_ctx* c) {
   if (!c->err) return DSO_OK;
-  int h = 0;
-  CK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int h[16] = {};
+  CK(cudaMemcpyAsync(h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (h != 0) {
-    CK(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
-    return fail(DSO_ETIMEOUT, "a kernel's bounded wait for its tile copy gave up (code " + std::to_string(h) + ")");
+  if (h[0] != 0) {
+    CK(cudaMemsetAsync(c->err, 0, sizeof(h), c->stream));
+    std::string ctx_info;
+    if (h[1])  // bounds-checked debug build: context of the first bad access
+      for (int i = 2; i < 10; ++i) ctx_info += " " + std::to_string(h[i]);
+    if (h[0] >= 100)
+      return fail(DSO_ECUDA, "bounds check failed in an axis pass (code " + std::to_string(h[0]) + ")" + ctx_info);
+    return fail(DSO_ETIMEOUT, "a kernel's bounded wait for its tile copy gave up (code " + std::to_string(h[0]) + ")");
   }
   return DSO_OK;
 }
@@ -770,7 +810,7 @@ dso_status dso_get_psi(dso_ctx* c, void* out, int where) {
     dso_status fs = check_device_flag(c);
     if (fs != DSO_OK) return fs;
   }
-  const size_t bytes = (size_t)c->S * c->P * c->esz();
+  const size_t bytes = (size_t)c->B * c->S * c->P * c->esz();
   CK(cudaMemcpyAsync(out, c->psi, bytes, where == DSO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                      c->stream));
   if (where == DSO_HOST) CK(cudaStreamSynchronize(c->stream));
@@ -795,43 +835,51 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
     CK(cudaMalloc(&c->Tax, h.size() * sizeof(double)));
     CK(cudaMemcpy(c->Tax, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
-  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->S * c->P * c->esz()));
+  if (!c->work) CK(cudaMalloc(&c->work, (size_t)c->B * c->S * c->P * c->esz()));
   if (!c->partials) CK(cudaMalloc(&c->partials, (size_t)obs_partial_blocks() * DSO_OBS_COLS * sizeof(double)));
-  if (!c->obs_out) CK(cudaMalloc(&c->obs_out, DSO_OBS_COLS * sizeof(double)));
+  if (!c->obs_out) CK(cudaMalloc(&c->obs_out, (size_t)c->B * DSO_OBS_COLS * sizeof(double)));
   // momentum representation of a copy: forward FFT along every axis
-  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->S * c->P * c->esz(), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->work, c->psi, (size_t)c->B * c->S * c->P * c->esz(), cudaMemcpyDeviceToDevice,
+                     c->stream));
   void* keep = c->psi;
   c->psi = c->work;
   cudaError_t e = cudaSuccess;
   for (int d = 0; d < c->D && e == cudaSuccess; ++d) e = run_pass(c, mkpass(d, 1, PASS_FWD));
   c->psi = keep;
   CK(e);
-  ObsArgs a;
-  a.psi = c->psi;
-  a.psik = c->work;
-  a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
-  a.V = c->V;
-  a.Tax = c->Tax;
-  for (int d = 0; d < 3; ++d) a.n[d] = c->n[d];
-  a.D = c->D;
-  a.S = c->S;
-  a.P = c->P;
-  CK(launch_observables(a, c->partials, c->obs_out, c->stream));
-  c->launches += 2;
-  double h[DSO_OBS_COLS];
-  CK(cudaMemcpyAsync(h, c->obs_out, (c->S + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  const int NPV = c->S * (c->S + 1) / 2;
+  for (int b = 0; b < c->B; ++b) {
+    ObsArgs a;
+    a.psi = at(c->psi, (size_t)b * c->S * c->P, c->esz());
+    a.psik = at(c->work, (size_t)b * c->S * c->P, c->esz());
+    a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
+    a.V = c->V + (size_t)b * NPV * c->P;
+    a.Tax = c->Tax;
+    for (int d = 0; d < 3; ++d) a.n[d] = c->n[d];
+    a.D = c->D;
+    a.S = c->S;
+    a.P = c->P;
+    CK(launch_observables(a, c->partials, c->obs_out + (size_t)b * DSO_OBS_COLS, c->stream));
+    c->launches += 2;
+  }
+  std::vector<double> h((size_t)c->B * DSO_OBS_COLS);
+  CK(cudaMemcpyAsync(h.data(), c->obs_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   double dV = 1.0;
   for (int d = 0; d < c->D; ++d) dV *= (c->qmax[d] - c->qmin[d]) / (double)c->n[d];
-  double tot = 0.0;
-  for (int s = 0; s < c->S; ++s) {
-    if (pops) pops[s] = h[s] * dV;
-    tot += h[s];
+  bool finite = true;
+  for (int b = 0; b < c->B; ++b) {
+    const double* hb = h.data() + (size_t)b * DSO_OBS_COLS;
+    double tot = 0.0;
+    for (int s = 0; s < c->S; ++s) {
+      if (pops) pops[(size_t)b * c->S + s] = hb[s] * dV;
+      tot += hb[s];
+    }
+    if (norm) norm[b] = std::sqrt(tot * dV);
+    if (energy) energy[b] = hb[c->S] * dV + hb[c->S + 1] * dV / (double)c->P;
+    finite = finite && std::isfinite(tot) && std::isfinite(hb[c->S]) && std::isfinite(hb[c->S + 1]);
   }
-  if (norm) *norm = std::sqrt(tot * dV);
-  if (energy) *energy = h[c->S] * dV + h[c->S + 1] * dV / (double)c->P;
-  if (!std::isfinite(tot) || !std::isfinite(h[c->S]) || !std::isfinite(h[c->S + 1]))
-    return fail(DSO_ENUMERIC, "non-finite observable");
+  if (!finite) return fail(DSO_ENUMERIC, "non-finite observable");
   return DSO_OK;
 }
 

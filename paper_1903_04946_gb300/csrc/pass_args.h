@@ -33,6 +33,21 @@ struct PassArgs {
   int* err;                // device flag set when a bounded wait gives up
   double tau2_scale;       // P: both kinetic tables carry 1/P, one inverse FFT runs
   int fp32;                // 1: complex arrays are float2 (FP32 storage mode)
+  int nbatch;              // independent jobs sharing the grid: psi is [nbatch][S][P]
+  long long u_batch_stride;  // elements between one job's potential tables and the next
+  // allocation extents (elements) for the bounds-checked debug build
+  const void* U_base;      // start of the potential tables
+  const void* tau_base;    // start of the kinetic tables
+  long long psi_elems, u_elems, tau_elems;
+};
+
+// Tile index -> (first staged surface over all jobs, job).  A pass staging
+// all S surfaces (SV = S) has nbatch * lines / G tiles; one staging a single
+// surface has nbatch * S * lines / G.
+struct TileJob {
+  long long tile;  // tile index within its line set
+  int surf0;       // first surface (counted over all jobs) of the tile
+  int job;
 };
 
 }  // namespace dso
