@@ -1,0 +1,144 @@
+"""Time to reach a wavefunction error of 1e-10 (the efficiency study of
+Sec. III, Figs. efficiency / pyrazine_efficiency), measured on the GPU.
+
+For a pyrazine-like three-surface model propagated to t_f, the error of a
+method at step dt is ||psi_dt(t_f) - psi_ref(t_f)|| (grid L2 norm, summed over
+surfaces), with psi_ref from Suzuki order 10 at a small step whose own
+convergence is checked by halving it.  For every composition scheme and
+order, dt = t_f / 2^k is halved until the error is <= 1e-10; the reported cost
+is the GPU time of that propagation.  The same is measured for a batch of B
+jobs of the same shape (their own potentials and packets) advanced together:
+the per-wavepacket time is the batch time divided by B.
+
+    python -m paper_1903_04946_gb300.efficiency [--grid 32] [--batch 32] [--tf 2000]
+
+Prints one JSON document.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import (DSO_SUZUKI, DSO_TRIPLE_JUMP, Context, dso_scheme_coefficients, dso_set_scheme)
+
+SCHEMES = [("triple_jump", 2), ("triple_jump", 4), ("triple_jump", 6), ("triple_jump", 8), ("triple_jump", 10),
+           ("suzuki", 4), ("suzuki", 6), ("suzuki", 8), ("suzuki", 10)]
+
+
+def _code(scheme):
+    return DSO_SUZUKI if scheme == "suzuki" else DSO_TRIPLE_JUMP
+
+
+def _timed_run(ctx, tf, dt):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.propagate(tf, dt)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def _propagate(problems, scheme, order, tf, k, batch):
+    ctx = Context()
+    if batch:
+        ctx.load_batch(problems)
+    else:
+        ctx.load_problem(problems[0])
+    dso_set_scheme(ctx.ctx, order, _code(scheme))
+    dt = tf / 2 ** k
+    ctx.propagate(dt, dt)          # tables, autotuning and graph capture, untimed
+    ctx.set_psi(np.stack([p.psi0 for p in problems]) if batch else problems[0].psi0)
+    secs = _timed_run(ctx, tf, dt)
+    psi = ctx.psi()
+    ctx.close()
+    return psi, secs
+
+
+def _err(problem, psi, ref):
+    dV = float(np.prod([(problem.qmax[d] - problem.qmin[d]) / problem.n[d] for d in range(problem.D)]))
+    return float(np.sqrt(np.sum(np.abs(psi - ref) ** 2) * dV))
+
+
+def study(grid=32, batch=32, tf=2000.0, target=1e-10, kmax=20, ref_k=7, seed=1904):
+    import synth
+    n = (grid, grid, grid)
+    base = synth.pyrazine_like(seed=seed, n=n)
+    # batch jobs share grid and masses: vary the couplings and packet, keep omega
+    jobs = [base]
+    for b in range(1, batch):
+        pr = synth.pyrazine_like(seed=seed + 1000 + b, n=n)
+        pr.mass = base.mass
+        jobs.append(pr)
+    out = {"model": f"pyrazine-like 3-D, 3 surfaces, {grid}^3 grid", "t_final": tf, "target": target,
+           "batch": batch}
+    # reference: Suzuki 10 at tf / 2^ref_k, checked against tf / 2^(ref_k+1)
+    ref_b, _ = _propagate(jobs, "suzuki", 10, tf, ref_k, True)
+    ref2_b, _ = _propagate(jobs, "suzuki", 10, tf, ref_k + 1, True)
+    out["reference"] = {"scheme": "suzuki", "order": 10, "dt": tf / 2 ** (ref_k + 1),
+                        "self_error": max(_err(jobs[b], ref_b[b], ref2_b[b]) for b in range(batch))}
+    ref = ref2_b
+    rows = []
+    for scheme, order in SCHEMES:
+        nsub = len(dso_scheme_coefficients(order, _code(scheme))[1])
+        row = {"scheme": scheme, "order": order, "substeps_per_step": nsub}
+        k = max(2, {2: 10, 4: 6, 6: 5, 8: 4, 10: 3}[order] - (1 if scheme == "suzuki" else 0))
+        found = None
+        while k <= kmax:
+            psi, secs = _propagate(jobs[:1], scheme, order, tf, k, False)
+            e = _err(jobs[0], psi[0] if psi.ndim == 5 else psi, ref[0])
+            if e <= target:
+                found = (k, e, secs)
+                break
+            if not np.isfinite(e) or e > 10:
+                k += 2
+            else:
+                # predicted k from the order: e ~ C dt^order
+                need = int(np.ceil(np.log2(e / target) / order))
+                k += max(1, min(need, 3))
+        if found is None:
+            row["reached"] = False
+            rows.append(row)
+            continue
+        k, e, secs = found
+        row.update(reached=True, k=k, dt=tf / 2 ** k, steps=2 ** k, error=e, single_seconds=secs)
+        # the batch shares one dt: halve it until every job meets the target
+        kb = k
+        while kb <= kmax:
+            psi_b, secs_b = _propagate(jobs, scheme, order, tf, kb, True)
+            worst = max(_err(jobs[b], psi_b[b], ref[b]) for b in range(batch))
+            if worst <= target:
+                break
+            kb += 1
+        row.update(batch_k=kb, batch_seconds=secs_b, batch_per_wavepacket_seconds=secs_b / batch,
+                   batch_max_error=worst, batch_reached=worst <= target)
+        rows.append(row)
+    out["methods"] = rows
+    done = [r for r in rows if r.get("reached")]
+    if done:
+        best = min(done, key=lambda r: r["single_seconds"])
+        o2 = next((r for r in done if r["order"] == 2), None)
+        out["best_single"] = {"scheme": best["scheme"], "order": best["order"], "seconds": best["single_seconds"]}
+        best_b = min((r for r in done if r.get("batch_reached")), key=lambda r: r["batch_per_wavepacket_seconds"])
+        out["best_batched_per_wavepacket"] = {"scheme": best_b["scheme"], "order": best_b["order"],
+                                              "seconds": best_b["batch_per_wavepacket_seconds"]}
+        out["batched_vs_single_speedup"] = best["single_seconds"] / best_b["batch_per_wavepacket_seconds"]
+        if o2:
+            out["best_vs_order2_speedup"] = o2["single_seconds"] / best["single_seconds"]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--tf", type=float, default=2000.0)
+    ap.add_argument("--kmax", type=int, default=20)
+    args = ap.parse_args()
+    print(json.dumps(study(args.grid, args.batch, args.tf, kmax=args.kmax)))
+
+
+if __name__ == "__main__":
+    main()
