@@ -160,6 +160,12 @@ dso_status dso_profile_steps(dso_ctx* ctx, double dt, int nsteps, int max_kinds,
                              int* flags, int* surfaces, int* launches_per_step, double* avg_ms,
                              int* tile_lines, int* variant);
 
+/* Non-blocking progress query: 1 while GPU work issued by this context is
+ * still pending on its stream, 0 when all of it has finished, a negative
+ * dso_status on error.  Lets a host loop serve many contexts without
+ * blocking on any one of them. */
+int dso_busy(const dso_ctx* ctx);
+
 /* Number of kernel launches this context has issued since creation
  * (diagnostics: counts each launch of the library's own kernels, including
  * those inside CUDA-graph replays). */

@@ -26,7 +26,7 @@ EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
-    "dso_position_observables_noalloc",
+    "dso_position_observables_noalloc", "dso_busy",
 )
 
 _lib = None
@@ -64,6 +64,7 @@ def load(path: str = LIB):
         "dso_scheme_coefficients": (i32, [i32, i32, pi, pi, pd, pd, pi, pi, pi, pi]),
         "dso_profile_steps": (i32, [vp, dbl, i32, i32, pi, pi, pi, pi, pi, pd, pi, pi]),
         "dso_launch_count": (i64, [vp]),
+        "dso_busy": (i32, [vp]),
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
     }
@@ -203,6 +204,13 @@ def dso_profile_steps(ctx, dt, nsteps, max_kinds=16):
                                  gl, var), "dso_profile_steps")
     return [dict(axis=ax[k], flags=fl[k], surfaces=sv[k], launches_per_step=cnt[k], avg_ms=ms[k],
                  tile_lines=gl[k], variant=var[k]) for k in range(min(nk.value, max_kinds))]
+
+
+def dso_busy(ctx) -> bool:
+    r = load().dso_busy(ctx)
+    if r < 0:
+        raise DSOError(r, "dso_busy")
+    return r == 1
 
 
 def dso_launch_count(ctx) -> int:

@@ -20,8 +20,11 @@
 #include <cstdlib>
 #include <cstring>
 #include <exception>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -432,8 +435,33 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 // real operator tables, and keep the fastest.  The FFT work per amplitude
 // does not depend on G; G trades load balance across the SMs (many small
 // CTAs) against per-CTA overhead.  Skipped when DSO_AUTOTUNE=0.
+// Tuning results are shared by every context of the process with the same
+// grid, surface count, batch, precision and elementary method, so that a
+// stream of jobs of one shape (a serving loop) tunes once.
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int>;
+struct TuneVal {
+  int G[DSO_MAX_DIM][2];
+  int variant[DSO_MAX_DIM][2];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+TuneKey tune_key(const dso_ctx* c) {
+  return TuneKey(c->D, c->n[0], c->n[1], c->n[2], c->S, c->B, c->prec, c->elementary, c->device);
+}
+
 dso_status autotune_tiles(dso_ctx* c) {
   if (c->tuned) return DSO_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(c));
+    if (it != g_tune_cache.end() && !getenv("DSO_VARIANT")) {
+      std::memcpy(c->G, it->second.G, sizeof(c->G));
+      std::memcpy(c->variant, it->second.variant, sizeof(c->variant));
+      c->tuned = true;
+      return DSO_OK;
+    }
+  }
   const char* env = getenv("DSO_AUTOTUNE");
   const char* fv0 = getenv("DSO_VARIANT");
   if (env && env[0] == '0' && !(fv0 && fv0[0])) {
@@ -516,6 +544,13 @@ dso_status autotune_tiles(dso_ctx* c) {
   if (e1) cudaEventDestroy(e1);
   CK(err);
   c->tuned = true;
+  if (!getenv("DSO_VARIANT")) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    TuneVal v;
+    std::memcpy(v.G, c->G, sizeof(v.G));
+    std::memcpy(v.variant, c->variant, sizeof(v.variant));
+    g_tune_cache[tune_key(c)] = v;
+  }
   return DSO_OK;
 }
 
@@ -973,6 +1008,15 @@ dso_status dso_profile_steps(dso_ctx* c, double dt, int nsteps, int max_kinds, i
     if (variant) variant[k] = c->variant[kinds[k].axis][which];
   }
   return DSO_OK;
+}
+
+int dso_busy(const dso_ctx* c) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  DeviceGuard g(c->device);
+  const cudaError_t e = cudaStreamQuery(c->stream);
+  if (e == cudaSuccess) return 0;
+  if (e == cudaErrorNotReady) return 1;
+  return fail(DSO_ECUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
 }
 
 int64_t dso_launch_count(const dso_ctx* c) { return c ? c->launches : 0; }

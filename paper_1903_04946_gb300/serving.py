@@ -1,0 +1,177 @@
+"""Continuous-batching serving loop for propagation jobs.
+
+Requests (a problem, a composition order, a final time and a step) arrive
+over time.  The loop keeps every admitted job's wavefunction, potential and
+operator tables resident on the device, admits waiting jobs as soon as their
+device-memory footprint fits the budget left by the jobs in flight, and
+advances every admitted job in chunks of time steps, each job on its own CUDA
+stream, so jobs admitted while others run overlap with them on the device.
+Finished jobs are read back, their latency (finish - arrival) recorded, and
+their memory returned to the budget for the next admission.
+
+All propagation work runs in the library's kernels through the C ABI; this
+module only schedules.  Chunking a propagation does not change its result:
+a chunk boundary applies the same operations in the same order as the pass
+that would have fused them.
+
+    python -m paper_1903_04946_gb300.serving [--jobs 48] [--load 0.8] [--budget-gb 8]
+
+prints one JSON document with p50/p99 latency and throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (DSO_FP64, DSO_TRIPLE_JUMP, Context, dso_busy, dso_scheme_coefficients, dso_set_scheme)
+
+
+@dataclass
+class Job:
+    jid: int
+    problem: object
+    order: int
+    t: float
+    dt: float
+    arrival: float = 0.0           # seconds after the start of the run
+    scheme: int = DSO_TRIPLE_JUMP
+    ctx: object = None
+    steps_total: int = 0
+    steps_done: int = 0
+    admitted: float = -1.0
+    finished: float = -1.0
+    footprint: int = 0
+    result: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def substeps(self) -> int:
+        return len(dso_scheme_coefficients(self.order, self.scheme)[1])
+
+
+def footprint_bytes(problem, order, scheme=DSO_TRIPLE_JUMP, esz=16) -> int:
+    """Device bytes one job holds: psi and the autotuning/observables work
+    copy, the FP64 potential, the potential unitaries (one per unique a~) and
+    kinetic phases (one per unique b~), twiddles and small buffers."""
+    S, P = problem.S, problem.points
+    NP = S * (S + 1) // 2
+    a, b, ia, ib, na, nb = dso_scheme_coefficients(order, scheme)
+    return int(2 * S * P * esz + NP * P * 8 + na * NP * P * esz + nb * P * esz + (1 << 20))
+
+
+def job_cost_seconds(job, rate=1.2e9) -> float:
+    """Rough GPU time of a job at `rate` grid-points x substeps per second
+    (per surface triple), used only to pick an arrival rate."""
+    return job.problem.points * job.problem.S / 3 * job.substeps * job.steps_total / rate
+
+
+class Server:
+    def __init__(self, device=0, budget_bytes=None, chunk_steps=16, precision=DSO_FP64):
+        import torch
+        self.device = device
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(device)
+            budget_bytes = int(0.8 * free)
+        self.budget = budget_bytes
+        self.used = 0
+        self.chunk_steps = chunk_steps
+        self.precision = precision
+
+    def _admit(self, job, now):
+        job.ctx = Context(device=self.device, precision=self.precision)
+        job.ctx.load_problem(job.problem)
+        dso_set_scheme(job.ctx.ctx, job.order, job.scheme)
+        job.admitted = now
+        self.used += job.footprint
+
+    def _retire(self, job, now):
+        job.result = job.ctx.psi()
+        job.ctx.close()
+        job.ctx = None
+        job.finished = now
+        self.used -= job.footprint
+
+    def run(self, jobs):
+        """Serve `jobs` (arrival times in seconds from now); returns stats."""
+        for j in jobs:
+            j.steps_total = int(round(j.t / j.dt))
+            j.footprint = footprint_bytes(j.problem, j.order, j.scheme, 8 if self.precision else 16)
+            if j.footprint > self.budget:
+                raise ValueError(f"job {j.jid} needs {j.footprint} bytes, more than the budget")
+        waiting = sorted(jobs, key=lambda j: j.arrival)
+        active = []
+        t0 = time.perf_counter()
+        max_active = 0
+        while waiting or active:
+            now = time.perf_counter() - t0
+            # admit arrived jobs in arrival order while their footprint fits
+            while waiting and waiting[0].arrival <= now and self.used + waiting[0].footprint <= self.budget:
+                job = waiting.pop(0)
+                self._admit(job, now)
+                active.append(job)
+            max_active = max(max_active, len(active))
+            progressed = False
+            for job in list(active):
+                if dso_busy(job.ctx.ctx):
+                    continue
+                if job.steps_done >= job.steps_total:
+                    self._retire(job, time.perf_counter() - t0)
+                    active.remove(job)
+                    progressed = True
+                    continue
+                k = min(self.chunk_steps, job.steps_total - job.steps_done)
+                job.ctx.propagate(k * job.dt, job.dt)   # asynchronous on the job's stream
+                job.steps_done += k
+                progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        lat = np.array([j.finished - j.arrival for j in jobs])
+        work = sum(j.problem.points * j.substeps * j.steps_total for j in jobs)
+        return {"jobs": len(jobs), "wall_seconds": wall, "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+                "throughput_grid_pts_substeps_per_s": work / wall, "max_concurrent_jobs": max_active,
+                "budget_bytes": self.budget}
+
+
+def make_jobs(n_jobs=48, seed=1907, load=0.8, max_points=1 << 21, rate=1.2e9):
+    """Seeded Poisson stream of mixed jobs; the arrival rate is set so that the
+    offered work is `load` times the GPU's rate."""
+    import synth
+    jobs = []
+    for i in range(n_jobs):
+        pr, order, t, dt = synth.serving_job(seed + i, max_points=max_points)
+        j = Job(jid=i, problem=pr, order=order, t=t, dt=dt)
+        j.steps_total = int(round(t / dt))
+        jobs.append(j)
+    mean_cost = float(np.mean([job_cost_seconds(j, rate) for j in jobs]))
+    lam = load / mean_cost
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_jobs))
+    for j, a in zip(jobs, arrivals):
+        j.arrival = float(a)
+    return jobs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--jobs", type=int, default=48)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--budget-gb", type=float, default=0.0)
+    ap.add_argument("--max-points", type=int, default=1 << 21)
+    ap.add_argument("--seed", type=int, default=1907)
+    args = ap.parse_args()
+    jobs = make_jobs(args.jobs, args.seed, args.load, args.max_points)
+    srv = Server(budget_bytes=int(args.budget_gb * 2 ** 30) if args.budget_gb else None)
+    stats = srv.run(jobs)
+    stats.update(load=args.load, seed=args.seed, max_points=args.max_points,
+                 workload="seeded Poisson stream: D in {1,2,3}, 2^8..2^21 points per surface, S in {2,3,4}, "
+                          "orders 2-8 (triple jump), t in [500, 5000] a.u., complex128")
+    print(json.dumps(stats))
+
+
+if __name__ == "__main__":
+    main()

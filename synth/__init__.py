@@ -259,3 +259,62 @@ def random_state(seed: int, like: Problem) -> np.ndarray:
             [(like.qmax[d] - like.qmin[d]) * rng.uniform(0.03, 0.06) for d in range(D)])
     dV = float(np.prod([(like.qmax[d] - like.qmin[d]) / like.n[d] for d in range(D)]))
     return psi / np.sqrt(np.sum(np.abs(psi) ** 2) * dV)
+
+
+# ---------------------------------------------------------------------------
+# Mixed job stream for a serving loop (shape of the serving configuration)
+# ---------------------------------------------------------------------------
+
+SERVING_DT = {2: 2.0, 4: 10.0, 6: 20.0, 8: 40.0}
+
+
+def serving_job(seed: int, max_points: int = 1 << 21, min_points: int = 1 << 8):
+    """One seeded propagation request: D in {1, 2, 3}, a power-of-two grid with
+    min_points..max_points points per surface (each axis 8..4096 points and
+    S * n_0 <= 8192), S in {2, 3, 4} surfaces with harmonic diagonals in
+    dimensionless normal coordinates (omega ~ U[0.005, 0.02], m = 1/omega)
+    plus seeded linear couplings, a displaced Gaussian on surface 1, order in
+    {2, 4, 6, 8} (triple jump), t ~ U[500, 5000] rounded to a multiple of
+    the order's dt (SERVING_DT).  Returns (problem, order, t, dt)."""
+    rng = np.random.default_rng(seed)
+    while True:
+        D = int(rng.integers(1, 4))
+        S = int(rng.integers(2, 5))
+        logp = int(rng.integers(int(np.log2(min_points)), int(np.log2(max_points)) + 1))
+        # split logp over D axes, each axis 2^3..2^12
+        parts = [3] * D
+        rest = logp - 3 * D
+        if rest < 0:
+            continue
+        for _ in range(rest):
+            cand = [i for i in range(D) if parts[i] < 12]
+            if not cand:
+                break
+            parts[int(rng.choice(cand))] += 1
+        n = tuple(2 ** p for p in parts)
+        if sum(parts) != logp or S * n[0] > 8192:
+            continue
+        break
+    omega = rng.uniform(0.005, 0.02, size=D)
+    extent = 7.0
+    qmin, qmax = tuple([-extent] * D), tuple([extent] * D)
+    Q = mesh(n, qmin, qmax)
+    V = np.zeros((S * (S + 1) // 2,) + n)
+    for r in range(S):
+        for c in range(r, S):
+            k = packed_index(r, c, S)
+            if r == c:
+                v = rng.uniform(0.0, 0.05) * np.ones(Q[0].shape) * r
+                for d in range(D):
+                    v = v + 0.5 * omega[d] * Q[d] ** 2 + rng.uniform(-0.01, 0.01) * Q[d]
+            else:
+                v = rng.uniform(0.002, 0.01) * Q[int(rng.integers(0, D))]
+            V[k] = v
+    psi0 = np.zeros((S,) + n, dtype=np.complex128)
+    psi0[0] = gaussian(n, qmin, qmax, rng.uniform(-1.0, 1.0, size=D), [0.0] * D, [1.0] * D)
+    order = int(rng.choice([2, 4, 6, 8]))
+    dt = SERVING_DT[order]
+    t = dt * max(1, int(round(rng.uniform(500.0, 5000.0) / dt)))
+    pr = Problem(n=n, qmin=qmin, qmax=qmax, mass=tuple(1.0 / omega), S=S, V=V, psi0=psi0,
+                 name=f"serving_{seed}", params=dict(seed=seed, omega=omega))
+    return pr, order, t, dt
