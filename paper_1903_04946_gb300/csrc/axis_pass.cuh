@@ -288,17 +288,24 @@ __device__ __forceinline__ void tile_elem(int e, const TileGeom& tg, int& g, int
 }
 
 // S x S complex matvec with the packed complex-symmetric unitary (entries
-// in C, products accumulated in C's precision).
+// in C, products accumulated in C's precision).  With dec0, surface 0 is
+// uncoupled from the others (its off-diagonal potential entries vanish on the
+// whole grid, as in the paper's pyrazine model), so U is block diagonal:
+// U_0c = 0 for c > 0 and those products are skipped.  The branch is uniform
+// across the launch.
 template <int SV, typename C>
-__device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], const C (&x)[SV], C (&y)[SV]) {
+__device__ __forceinline__ void matvec_rows(const C (&u)[SV * (SV + 1) / 2], const C (&x)[SV], C (&y)[SV],
+                                            int r0) {
 #pragma unroll
   for (int r = 0; r < SV; ++r) {
+    if (r < r0) continue;
     C acc = mkc((RealT<C>)0, (RealT<C>)0);
 #pragma unroll
     for (int c = 0; c < SV; ++c) {
+      if (c < r0) continue;
       const int lo = r < c ? r : c, hi = r < c ? c : r;
       const int k = lo * SV - lo * (lo - 1) / 2 + (hi - lo);
-      if (c == 0) {
+      if (c == r0) {
         acc = cmul(u[k], x[c]);
       } else {
         acc.x = fma(u[k].x, x[c].x, acc.x);
@@ -308,6 +315,17 @@ __device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], cons
       }
     }
     y[r] = acc;
+  }
+}
+
+template <int SV, typename C>
+__device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], const C (&x)[SV], C (&y)[SV],
+                                           int dec0 = 0) {
+  if (SV > 2 && dec0) {
+    y[0] = cmul(u[0], x[0]);
+    matvec_rows<SV>(u, x, y, 1);
+  } else {
+    matvec_rows<SV>(u, x, y, 0);
   }
 }
 
@@ -335,6 +353,7 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
                                                 const PassArgs* dbg = nullptr) {
   constexpr int NP = SV * (SV + 1) / 2;
   const int tile_pts = G * L;
+  const int dec0 = dbg ? dbg->dec0 : 0;
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
@@ -345,6 +364,10 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
     for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + off];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
+      if (SV > 2 && dec0 && k >= 1 && k < SV) {  // U_0c = 0: not loaded
+        u[k] = mkc((RealT<C>)0, (RealT<C>)0);
+        continue;
+      }
 #ifdef DSO_DEBUG_BOUNDS
       if (dbg) {
         const long long off = (long long)(&U[(size_t)k * P + gi] - (const C*)dbg->U_base);
@@ -356,7 +379,7 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
 #endif
       u[k] = __ldg(&U[(size_t)k * P + gi]);
     }
-    matvec_sym<SV>(u, x, y);
+    matvec_sym<SV>(u, x, y, dec0);
 #pragma unroll
     for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + off] = y[s];
   }

@@ -117,7 +117,8 @@ __device__ __forceinline__ void pq_issue(double2* dst, const double2* src, int c
 }
 
 template <int SV>
-__device__ __forceinline__ void pq_potential(double2* sm, const double2* ub, int tile_pts, int tid, int nthr) {
+__device__ __forceinline__ void pq_potential(double2* sm, const double2* ub, int tile_pts, int tid, int nthr,
+                                             int dec0) {
   constexpr int NP = SV * (SV + 1) / 2;
 #pragma unroll 1
   for (int e = tid; e < tile_pts; e += nthr) {
@@ -125,8 +126,9 @@ __device__ __forceinline__ void pq_potential(double2* sm, const double2* ub, int
 #pragma unroll
     for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + e];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) u[k] = ub[(size_t)k * tile_pts + e];
-    matvec_sym<SV>(u, x, y);
+    for (int k = 0; k < NP; ++k)
+      u[k] = (SV > 2 && dec0 && k >= 1 && k < SV) ? make_double2(0.0, 0.0) : ub[(size_t)k * tile_pts + e];
+    matvec_sym<SV>(u, x, y, dec0);
 #pragma unroll
     for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + e] = y[s];
   }
@@ -200,10 +202,10 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
       __syncthreads();
       // table and psi buffers share the [g][n] order, so pq_potential walks
       // both with one flat index
-      pq_potential<SV>(x, tb, tile_pts, tid, nthr);
+      pq_potential<SV>(x, tb, tile_pts, tid, nthr, a.dec0);
       __syncthreads();
       if (a.U2) {
-        apply_potential<L, SV>(x, (const double2*)a.U2 + t.uoff, t.tg, G, a.stride, a.P, tid, nthr);
+        apply_potential<L, SV>(x, (const double2*)a.U2 + t.uoff, t.tg, G, a.stride, a.P, tid, nthr, &a);
       }
       if (a.flags & PASS_T) {  // 1-D grids: the kinetic phase follows in this pass
         pq_issue<L>(tb, (const double2*)a.tau, 1, a.P, t, G, a.stride, tid, nthr);

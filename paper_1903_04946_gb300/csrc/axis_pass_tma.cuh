@@ -140,15 +140,17 @@ __device__ __forceinline__ void tma_fft(double2* sm, const double2* tws, int G, 
 }
 
 template <int SV>
-__device__ __forceinline__ void tma_potential(double2* x, const double2* ub, int tile_pts, int tid, int nthr) {
+__device__ __forceinline__ void tma_potential(double2* x, const double2* ub, int tile_pts, int tid, int nthr,
+                                              int dec0) {
   constexpr int NP = SV * (SV + 1) / 2;
   for (int e = tid; e < tile_pts; e += nthr) {
     double2 xs[SV], y[SV], u[NP];
 #pragma unroll
     for (int s = 0; s < SV; ++s) xs[s] = x[(size_t)s * tile_pts + e];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) u[k] = ub[(size_t)k * tile_pts + e];
-    matvec_sym<SV>(u, xs, y);
+    for (int k = 0; k < NP; ++k)
+      u[k] = (SV > 2 && dec0 && k >= 1 && k < SV) ? make_double2(0.0, 0.0) : ub[(size_t)k * tile_pts + e];
+    matvec_sym<SV>(u, xs, y, dec0);
 #pragma unroll
     for (int s = 0; s < SV; ++s) x[(size_t)s * tile_pts + e] = y[s];
   }
@@ -159,7 +161,7 @@ __device__ __forceinline__ void tma_potential(double2* x, const double2* ub, int
 template <int L, int SV>
 __device__ __forceinline__ void tma_potential_global(double2* x, const double2* __restrict__ U, const PassArgs& a,
                                                      long long o0, long long i0, int Wi_log2, int tile_pts, int tid,
-                                                     int nthr) {
+                                                     int nthr, int dec0 = 0) {
   constexpr int NP = SV * (SV + 1) / 2;
   const int Wi = 1 << Wi_log2;
   for (int e = tid; e < tile_pts; e += nthr) {
@@ -171,8 +173,9 @@ __device__ __forceinline__ void tma_potential_global(double2* x, const double2* 
 #pragma unroll
     for (int s = 0; s < SV; ++s) xs[s] = x[(size_t)s * tile_pts + e];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) u[k] = __ldg(&U[(size_t)k * a.P + gi]);
-    matvec_sym<SV>(u, xs, y);
+    for (int k = 0; k < NP; ++k)
+      u[k] = (SV > 2 && dec0 && k >= 1 && k < SV) ? make_double2(0.0, 0.0) : __ldg(&U[(size_t)k * a.P + gi]);
+    matvec_sym<SV>(u, xs, y, dec0);
 #pragma unroll
     for (int s = 0; s < SV; ++s) x[(size_t)s * tile_pts + e] = y[s];
   }
@@ -270,11 +273,11 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
       if (tid == 0) atomicExch(a.err, 2);
       return;
     }
-    tma_potential<SV>(x, tb, tile_pts, tid, nthr);
+    tma_potential<SV>(x, tb, tile_pts, tid, nthr, a.dec0);
     __syncthreads();
     if (a.U2) {
       tma_potential_global<L, SV>(x, (const double2*)a.U2 + (size_t)tj.job * a.u_batch_stride, a, tg.o0, tg.i0,
-                                  Wi_log2, tile_pts, tid, nthr);
+                                  Wi_log2, tile_pts, tid, nthr, a.dec0);
       __syncthreads();
     }
     if (tstep && tid == 0) {  // 1-D grids: kinetic phases into the freed table buffer
@@ -325,6 +328,201 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
     tma_store_5d(&maps.psi, 0, c1, 0, c3, surf0, x);
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Persistent form (variant 3).  The one-tile-per-CTA kernel above runs the
+// whole grid in about one wave on the wavefunction sizes of interest, so all
+// CTAs load at the same time, then all compute, then all store: the FP64
+// pipe idles during the first and last phase.  Here a grid of a few CTAs per
+// SM takes tiles from the per-launch queue (the two counters the persistent
+// cp.async variant uses, left zeroed by the last CTA out), and every CTA
+// double-buffers: while tile t is transformed in one stage buffer, the TMA
+// engine fills the other with tile t+1 (wavefunction and table), and tile t
+// leaves with a bulk tensor store that the next prefetch into that buffer
+// waits for.  The arithmetic is that of axis_pass_tma_kernel, in the same
+// order, so both variants give identical results.
+//
+// Passes that apply both a potential and a kinetic phase (1-D grids) are
+// not handled here; the host does not select this variant for them.
+//
+// Shared memory: two stages of [psi SV*G*L][table np*G*L] (np = 0 when the
+// pass has no table step), the twiddles, three mbarriers and a status word.
+template <int L, int SV>
+inline size_t tmap_smem_bytes(int G, bool has_tab) {
+  const int np = has_tab ? tma_np_tab<L, SV>() : 0;
+  return 2 * (size_t)(SV + np) * G * L * 16 + (size_t)L * 16 + 128 + 64;
+}
+
+template <int L, int SV>
+__global__ void __launch_bounds__(256) axis_pass_tmap_kernel(PassArgs a, const __grid_constant__ TmaMaps maps,
+                                                             unsigned* __restrict__ queue) {
+  extern __shared__ double2 sm_raw[];
+  double2* sm = (double2*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
+  __shared__ long long s_tile[2];
+  __shared__ volatile int s_zero;
+  constexpr int NP = SV * (SV + 1) / 2;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int G = a.G;
+  const int tile_pts = G * L;
+  const int nslots = SV * G * (L / 8);
+  const bool vstep = (SV > 1) && (a.U1 != nullptr);
+  const bool tstep = (a.flags & PASS_T) != 0;
+  const bool has_tab = vstep || tstep;
+  const int np_tab = has_tab ? (vstep ? NP : 1) : 0;
+  const int stage_elems = (SV + (has_tab ? tma_np_tab<L, SV>() : 0)) * tile_pts;
+  double2* stage0 = sm;
+  double2* tws = sm + 2 * (size_t)stage_elems;
+  unsigned long long* bar = (unsigned long long*)(tws + L);  // [0], [1]: stages; [2]: twiddles
+  volatile int* status = (volatile int*)(bar + 3);
+  const long long ntiles = (SV == a.S) ? (long long)a.nbatch * (a.lines >> a.G_log2)
+                                       : (long long)a.nbatch * a.S * (a.lines >> a.G_log2);
+  const unsigned tab_bytes = (unsigned)(np_tab * tile_pts * sizeof(double2));
+  const unsigned psi_bytes = (unsigned)(SV * tile_pts * sizeof(double2));
+
+  // thread 0: start the copies of tile `tile` into stage buffer `st`
+  auto issue = [&](long long tile, double2* st, unsigned long long* b) {
+    const TileJob tj = split_tile(tile, SV, a);
+    const TileGeom tg = make_geom(tj.tile, a);
+    mbar_expect_tx(b, psi_bytes + tab_bytes);
+    tma_load_5d(st, &maps.psi, 0, (int)tg.i0, 0, (int)tg.o0, tj.surf0, b);
+    if (vstep) {
+      tma_load_5d(st + (size_t)SV * tile_pts, &maps.tab, 0, (int)tg.i0, 0, (int)tg.o0,
+                  (int)((long long)tj.job * a.u_batch_stride / a.P) + a.ua * NP, b);
+    } else if (tstep) {
+      tma_load_5d(st + (size_t)SV * tile_pts, &maps.tab, 0, (int)tg.i0, 0, (int)tg.o0, a.ub, b);
+    }
+  };
+
+  if (tid == 0) {
+    s_zero = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar[2], (unsigned)(L * sizeof(double2)));
+    bulk_load(tws, a.tw, (unsigned)(L * sizeof(double2)), &bar[2]);
+    const long long t0 = (long long)atomicAdd(&queue[0], 1u);
+    s_tile[0] = t0;
+    if (t0 < ntiles) issue(t0, stage0, &bar[0]);
+  }
+  // pending bit b (b < 2): a copy into stage b is in flight; bit 2: twiddles
+  unsigned pending = (tid == 0 && s_tile[0] < ntiles) ? 5u : 4u;
+  bool ok = cta_wait(&bar[2], 0, status, tid);
+  if (ok) pending &= ~4u;
+  long long cur = s_tile[0];
+  int s = 0;
+  unsigned phase = 0;  // bit b: parity of the next completion of stage b
+  while (ok && cur < ntiles) {
+    double2* x = stage0 + (size_t)s * stage_elems;
+    double2* tb = x + (size_t)SV * tile_pts;
+    if (tid == 0) {  // prefetch the next tile into the other stage
+      const long long nxt = (long long)atomicAdd(&queue[0], 1u);
+      s_tile[s ^ 1] = nxt;
+      if (nxt < ntiles) {
+        // the other stage's last store must have read its buffer
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        issue(nxt, stage0 + (size_t)(s ^ 1) * stage_elems, &bar[s ^ 1]);
+        pending |= 1u << (s ^ 1);
+      }
+    }
+    if (!cta_wait(&bar[s], (phase >> s) & 1u, status, tid)) {
+      ok = false;
+      break;
+    }
+    pending &= ~(1u << s);
+    phase ^= 1u << s;
+    const TileJob tj = split_tile(cur, SV, a);
+    const TileGeom tg = make_geom(tj.tile, a);
+    // Every shared-memory address of the tile work below depends only on the
+    // thread index and launch constants.  Left visible, the compiler keeps
+    // the addresses of one FFT call live for the next ones and across tiles,
+    // and spills.  Each FFT call therefore gets its arguments offset by a
+    // zero read from shared memory, which no compiler stage can fold.
+#define DSO_TMAP_FFT(INV)                                                                               \
+  do {                                                                                                  \
+    const int z = s_zero;                                                                               \
+    tma_fft<L, INV>(x + z, tws + z, G + z, tg.Wi_log2 + z, nslots + z, tid + z, nthr + z);              \
+  } while (0)
+    const int Wi_log2 = tg.Wi_log2;
+
+    if (a.flags & PASS_INV_FIRST) {
+      DSO_TMAP_FFT(true);
+      __syncthreads();
+    }
+    if (vstep) {
+      tma_potential<SV>(x, tb, tile_pts, tid, nthr, a.dec0);
+      __syncthreads();
+      if (a.U2) {
+        tma_potential_global<L, SV>(x, (const double2*)a.U2 + (size_t)tj.job * a.u_batch_stride, a, tg.o0, tg.i0,
+                                    Wi_log2, tile_pts, tid, nthr, a.dec0);
+        __syncthreads();
+      }
+    }
+    if (a.flags & PASS_FWD) DSO_TMAP_FFT(false);
+    if (tstep) {
+      __syncthreads();
+      for (int e = tid; e < tile_pts; e += nthr) {
+        const double2 ph = tb[e];
+#pragma unroll
+        for (int q = 0; q < SV; ++q) {
+          double2* p = &x[(size_t)q * tile_pts + e];
+          *p = cmul(*p, ph);
+        }
+      }
+      __syncthreads();
+      if (a.tau2) {  // second kinetic phase of a step boundary, from global memory
+        const int Wi = 1 << Wi_log2;
+        for (int e = tid; e < tile_pts; e += nthr) {
+          const int i = e & (Wi - 1);
+          const int n = (e >> Wi_log2) & (L - 1);
+          const int o = e >> (Wi_log2 + Plan<L>::log2L);
+          const long long gi = (((tg.o0 + o) * L + n) << a.stride_log2) + tg.i0 + i;
+          double2 ph = __ldg(&((const double2*)a.tau2)[gi]);
+          ph = cscale(ph, a.tau2_scale);
+#pragma unroll
+          for (int q = 0; q < SV; ++q) {
+            double2* p = &x[(size_t)q * tile_pts + e];
+            *p = cmul(*p, ph);
+          }
+        }
+        __syncthreads();
+      }
+      DSO_TMAP_FFT(true);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_5d(&maps.psi, 0, (int)tg.i0, 0, (int)tg.o0, tj.surf0, x);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    cur = s_tile[s ^ 1];
+    s ^= 1;
+  }
+#undef DSO_TMAP_FFT
+  if (tid == 0) {
+    if (!ok) {
+      // a bounded wait gave up: record it and let every copy this CTA
+      // started land before the CTA leaves (each wait again bounded)
+      atomicExch(a.err, 4);
+      if (pending & 1u) mbar_wait(&bar[0], phase & 1u);
+      if (pending & 2u) mbar_wait(&bar[1], (phase >> 1) & 1u);
+      if (pending & 4u) mbar_wait(&bar[2], 0);
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    // the last CTA out resets the queue for the next launch
+    __threadfence();
+    const unsigned done = atomicAdd(&queue[1], 1u);
+    if (done == gridDim.x - 1) {
+      queue[0] = 0u;
+      queue[1] = 0u;
+      __threadfence();
+    }
   }
 }
 

@@ -98,6 +98,7 @@ struct dso_ctx {
   // model and state
   int B = 1;                 // independent jobs sharing grid, masses and scheme
   int S = 0;
+  int dec0 = 0;              // surface 0 uncoupled in every job (block-diagonal potential)
   int prec = DSO_FP64;       // DSO_FP64: complex128 storage; DSO_FP32: complex64
   double* V = nullptr;       // packed [S(S+1)/2][P], always FP64
   void* psi = nullptr;       // [S][P] complex in the context's precision
@@ -125,6 +126,7 @@ struct dso_ctx {
   // tile lines and kernel variant per (axis, surfaces staged: 1 or S)
   int G[DSO_MAX_DIM][2] = {};
   int variant[DSO_MAX_DIM][2] = {};
+  int cps[DSO_MAX_DIM][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
   unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
   int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
@@ -250,12 +252,15 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.psi_elems = (long long)c->B * c->S * c->P;
   a.u_elems = (long long)c->B * c->n_vtab * NP * c->P;
   a.tau_elems = (long long)c->n_ttab * c->P;
+  a.dec0 = c->dec0;
+  a.ctas_per_sm = c->cps[p.axis][which];
   const long long ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G)
                                           : (long long)c->B * c->S * (a.lines / a.G);
   const int variant = c->variant[p.axis][which];
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
-  if (variant == 2) {
+  if (variant == 3 && p.u1 >= 0 && p.tb >= 0) return cudaErrorInvalidConfiguration;  // 1-D passes
+  if (variant == 2 || variant == 3) {
     const int Wi = (int)(stride < a.G ? stride : a.G);
     const int Go = a.G / Wi;
     const int NP = c->S * (c->S + 1) / 2;
@@ -442,6 +447,7 @@ using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, i
 struct TuneVal {
   int G[DSO_MAX_DIM][2];
   int variant[DSO_MAX_DIM][2];
+  int cps[DSO_MAX_DIM][2];
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -458,6 +464,7 @@ dso_status autotune_tiles(dso_ctx* c) {
     if (it != g_tune_cache.end() && !getenv("DSO_VARIANT")) {
       std::memcpy(c->G, it->second.G, sizeof(c->G));
       std::memcpy(c->variant, it->second.variant, sizeof(c->variant));
+      std::memcpy(c->cps, it->second.cps, sizeof(c->cps));
       c->tuned = true;
       return DSO_OK;
     }
@@ -483,6 +490,9 @@ dso_status autotune_tiles(dso_ctx* c) {
   for (const Pass& q : step_passes(c, false)) plan.push_back(q);
   for (const Pass& q : final_passes(c)) plan.push_back(q);
   std::vector<Pass> reps;
+  bool both[DSO_MAX_DIM][2] = {};  // some pass of the kind applies a potential and a kinetic phase (1-D)
+  for (const Pass& q : plan)
+    if (q.u1 >= 0 && q.tb >= 0) both[q.axis][q.SV == 1 ? 0 : 1] = true;
   for (const Pass& q : plan) {
     bool seen = false;
     for (const Pass& r : reps)
@@ -503,39 +513,54 @@ dso_status autotune_tiles(dso_ctx* c) {
       for (long long G = 1; G <= gmax && G <= lines; G *= 2)
         if ((SV * G * (L / 8)) % 32 == 0) any_whole = true;
       float best = 1e30f;
-      int bestG = c->G[d][which], bestV = c->variant[d][which];
+      int bestG = c->G[d][which], bestV = c->variant[d][which], bestC = c->cps[d][which];
       // DSO_VARIANT=v restricts the search to one kernel variant (testing)
       const char* fv = getenv("DSO_VARIANT");
-      const int only = (fv && fv[0] >= '0' && fv[0] <= '2') ? fv[0] - '0' : -1;
-      for (int var = 0; var < 3 && err == cudaSuccess; ++var) {
+      const int only = (fv && fv[0] >= '0' && fv[0] <= '3') ? fv[0] - '0' : -1;
+      const bool both_tables = both[d][which];
+      for (int var = 0; var < 4 && err == cudaSuccess; ++var) {
         if (only >= 0 && var != only) continue;
+        if (var != 0 && c->prec == DSO_FP32) continue;  // the other variants are FP64 only
+        if (var == 3 && both_tables) continue;
         for (long long G = 1; G <= gmax && G <= lines && err == cudaSuccess; G *= 2) {
           if (any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
-          if (var != 0 && c->prec == DSO_FP32) continue;  // the other variants are FP64 only
           if (var == 1 && !axis_pass_pq_supported(L, SV, (int)G)) continue;
           if (var == 2 && !axis_pass_tma_supported(L, SV, (int)G)) continue;
-          c->G[d][which] = (int)G;
-          c->variant[d][which] = var;
-          err = run_pass(c, p);  // warm-up
-          if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-          for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_pass(c, p);
-          if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-          float ms = 0.f;
-          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-          if (err == cudaSuccess && ms < best) {
-            best = ms;
-            bestG = (int)G;
-            bestV = var;
+          if (var == 3 && !axis_pass_tmap_supported(L, SV, (int)G)) continue;
+          // persistent TMA: also the number of resident CTAs per SM
+          static const int cps_try[4] = {0, 8, 4, 2};
+          for (int ci = 0; ci < (var == 3 ? 4 : 1) && err == cudaSuccess; ++ci) {
+            c->G[d][which] = (int)G;
+            c->variant[d][which] = var;
+            c->cps[d][which] = var == 3 ? cps_try[ci] : 0;
+            err = run_pass(c, p);  // warm-up
+            if (err == cudaErrorInvalidConfiguration) {  // does not fit (e.g. registers): not a candidate
+              (void)cudaGetLastError();
+              err = cudaSuccess;
+              continue;
+            }
+            if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_pass(c, p);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err == cudaSuccess && ms < best) {
+              best = ms;
+              bestG = (int)G;
+              bestV = var;
+              bestC = c->cps[d][which];
+            }
+            const char* vb = getenv("DSO_TUNE_VERBOSE");
+            if (vb && vb[0] == '1' && err == cudaSuccess)
+              fprintf(stderr, "dso autotune: axis %d SV %d flags %d variant %d G %lld cps %d: %.2f us\n", d, SV,
+                      p.flags, var, G, c->cps[d][which], ms * 1000.f / 3.f);
           }
-          const char* vb = getenv("DSO_TUNE_VERBOSE");
-          if (vb && vb[0] == '1' && err == cudaSuccess)
-            fprintf(stderr, "dso autotune: axis %d SV %d flags %d variant %d G %lld: %.2f us\n", d, SV, p.flags, var,
-                    G, ms * 1000.f / 3.f);
         }
       }
       c->G[d][which] = bestG;
       c->variant[d][which] = bestV;
+      c->cps[d][which] = bestC;
     }
   }
   c->psi = keep;
@@ -549,6 +574,7 @@ dso_status autotune_tiles(dso_ctx* c) {
     TuneVal v;
     std::memcpy(v.G, c->G, sizeof(v.G));
     std::memcpy(v.variant, c->variant, sizeof(v.variant));
+    std::memcpy(v.cps, c->cps, sizeof(v.cps));
     g_tune_cache[tune_key(c)] = v;
   }
   return DSO_OK;
@@ -707,6 +733,29 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   CK(cudaMemcpyAsync(c->V, V, count * sizeof(double), where == DSO_HOST ? cudaMemcpyHostToDevice
                                                                          : cudaMemcpyDeviceToDevice, c->stream));
   CK(cudaMalloc(&c->psi, (size_t)c->B * S * c->P * c->esz()));
+  // Surface 0 uncoupled (V_0c = 0 on the whole grid for c > 0, in every job):
+  // then U = exp(-i V t) is block diagonal and the V step skips U_0c.
+  {
+    std::vector<double> hv;
+    const double* vh = V;
+    if (where == DSO_DEVICE) {
+      hv.resize(count);
+      CK(cudaMemcpy(hv.data(), V, count * sizeof(double), cudaMemcpyDeviceToHost));
+      vh = hv.data();
+    }
+    int dec = S > 2 ? 1 : 0;
+    const size_t NPc = (size_t)S * (S + 1) / 2;
+    for (int b = 0; b < c->B && dec; ++b)
+      for (int k = 1; k < S && dec; ++k) {  // packed (0, k) sits at index k
+        const double* row = vh + ((size_t)b * NPc + k) * c->P;
+        for (long long g = 0; g < c->P; ++g)
+          if (row[g] != 0.0) {
+            dec = 0;
+            break;
+          }
+      }
+    c->dec0 = dec;
+  }
   if (!c->queue) {
     CK(cudaMalloc(&c->queue, 2 * sizeof(unsigned)));
     CK(cudaMemsetAsync(c->queue, 0, 2 * sizeof(unsigned), c->stream));
@@ -1043,6 +1092,13 @@ bool axis_pass_tma_supported(int L, int SV, int G) {
   if (!axis_pass_supported(L, SV) || L > 256) return false;
   const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
   const long long smem = (long long)(SV + np) * G * L * 16 + (long long)L * 16 + 192;
+  return SV * G * (L / 8) <= 256 && smem <= 220 * 1024 && encode_fn() != nullptr;
+}
+
+bool axis_pass_tmap_supported(int L, int SV, int G) {
+  if (!axis_pass_supported(L, SV) || L > 256) return false;
+  const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
+  const long long smem = 2LL * (SV + np) * G * L * 16 + (long long)L * 16 + 192;
   return SV * G * (L / 8) <= 256 && smem <= 220 * 1024 && encode_fn() != nullptr;
 }
 

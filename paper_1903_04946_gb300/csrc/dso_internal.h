@@ -33,11 +33,14 @@ struct TmaMaps;
 // with a tile queue and cp.async prefetch (axis_pass_pq.cuh), which needs
 // `queue` (two zeroed unsigned counters owned by the caller's context);
 // variant 2: one CTA per tile with TMA tile and table movement
-// (axis_pass_tma.cuh), which needs the tensor maps in `maps`.
+// (axis_pass_tma.cuh), which needs the tensor maps in `maps`; variant 3:
+// persistent CTAs with double-buffered TMA movement (axis_pass_tma.cuh),
+// which needs both `queue` and `maps`.
 cudaError_t launch_axis_pass(int L, int SV, int variant, const PassArgs& args, long long ntiles, unsigned* queue,
                              const TmaMaps* maps, cudaStream_t st);
 bool axis_pass_pq_supported(int L, int SV, int G);
 bool axis_pass_tma_supported(int L, int SV, int G);
+bool axis_pass_tmap_supported(int L, int SV, int G);
 // per-SV launchers (one translation unit each)
 cudaError_t launch_axis_pass_sv1(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
                                  const TmaMaps* maps, cudaStream_t st);

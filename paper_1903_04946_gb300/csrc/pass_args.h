@@ -39,6 +39,8 @@ struct PassArgs {
   const void* U_base;      // start of the potential tables
   const void* tau_base;    // start of the kinetic tables
   long long psi_elems, u_elems, tau_elems;
+  int dec0;                // surface 0 uncoupled (block-diagonal potential): skip its zero products
+  int ctas_per_sm;         // host side, persistent variants: resident CTAs per SM (0: as many as fit)
 };
 
 // Tile index -> (first staged surface over all jobs, job).  A pass staging

@@ -83,6 +83,38 @@ cudaError_t launch_tma(const PassArgs& a, const TmaMaps* maps, long long ntiles,
   return cudaGetLastError();
 }
 
+// Persistent TMA variant: a grid of min(ntiles, CTAs per SM x SMs) CTAs
+// drains the tile queue.
+template <int L, int SV>
+cudaError_t launch_tmap(const PassArgs& a, const TmaMaps* maps, long long ntiles, unsigned* queue, cudaStream_t st) {
+  static bool attr_set[64] = {};
+  static int nsm[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const int threads = SV * a.G * (L / 8);
+  const bool has_tab = (SV > 1 && a.U1) || (a.flags & PASS_T);
+  if ((SV > 1 && a.U1) && (a.flags & PASS_T)) return cudaErrorInvalidConfiguration;  // 1-D passes
+  const size_t smem = tmap_smem_bytes<L, SV>(a.G, has_tab);
+  if (threads > 256 || smem > 220 * 1024 || !maps || !queue) return cudaErrorInvalidConfiguration;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(axis_pass_tmap_kernel<L, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         220 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, axis_pass_tmap_kernel<L, SV>, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
+  long long grid = (long long)per_sm * nsm[dev];
+  if (grid > ntiles) grid = ntiles;
+  axis_pass_tmap_kernel<L, SV><<<(unsigned)grid, threads, smem, st>>>(a, *maps, queue);
+  return cudaGetLastError();
+}
+
 template <int L, int SV>
 cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, unsigned* queue, const TmaMaps* maps,
                            cudaStream_t st) {
@@ -93,6 +125,10 @@ cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, uns
   }
   if (variant == 2) {
     if constexpr (L <= 256 && SV * L / 8 <= 256) return launch_tma<L, SV>(a, maps, ntiles, st);
+    return cudaErrorInvalidConfiguration;
+  }
+  if (variant == 3) {
+    if constexpr (L <= 256 && SV * L / 8 <= 256) return launch_tmap<L, SV>(a, maps, ntiles, queue, st);
     return cudaErrorInvalidConfiguration;
   }
   return launch_one<L, SV>(a, ntiles, st);

@@ -77,6 +77,7 @@ class Server:
             budget_bytes = int(0.8 * free)
         self.budget = budget_bytes
         self.used = 0
+        self.peak_used = 0
         self.chunk_steps = chunk_steps
         self.precision = precision
 
@@ -86,6 +87,7 @@ class Server:
         dso_set_scheme(job.ctx.ctx, job.order, job.scheme)
         job.admitted = now
         self.used += job.footprint
+        self.peak_used = max(self.peak_used, self.used)
 
     def _retire(self, job, now):
         job.result = job.ctx.psi()
@@ -134,7 +136,7 @@ class Server:
         return {"jobs": len(jobs), "wall_seconds": wall, "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
                 "throughput_grid_pts_substeps_per_s": work / wall, "max_concurrent_jobs": max_active,
-                "budget_bytes": self.budget}
+                "budget_bytes": self.budget, "peak_footprint_bytes": self.peak_used}
 
 
 def make_jobs(n_jobs=48, seed=1907, load=0.8, max_points=1 << 21, rate=1.2e9):

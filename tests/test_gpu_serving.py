@@ -43,8 +43,14 @@ def test_admission_respects_budget():
     jobs = serving.make_jobs(n_jobs=8, seed=5, load=8.0, max_points=1 << 12)
     for j in jobs:
         j.t = j.dt * min(int(round(j.t / j.dt)), 10)
-    biggest = max(serving.footprint_bytes(j.problem, j.order, j.scheme) for j in jobs)
-    srv = serving.Server(budget_bytes=2 * biggest, chunk_steps=5)
+    fps = [serving.footprint_bytes(j.problem, j.order, j.scheme) for j in jobs]
+    # the biggest job fits only alone
+    budget = max(fps) + min(fps) - 1
+    srv = serving.Server(budget_bytes=budget, chunk_steps=5)
     stats = srv.run(jobs)
-    assert stats["max_concurrent_jobs"] <= 2
+    assert stats["peak_footprint_bytes"] <= budget
+    big = jobs[int(np.argmax(fps))]
+    for j in jobs:
+        if j is not big:
+            assert j.finished <= big.admitted or big.finished <= j.admitted, j.jid
     assert all(j.result is not None and np.all(np.isfinite(j.result)) for j in jobs)

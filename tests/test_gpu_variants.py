@@ -1,7 +1,9 @@
 """Parity of every axis-pass kernel variant against the oracle.  The
 autotuner normally picks the fastest; DSO_VARIANT forces one: 0 one CTA per
 tile with per-thread loads, 1 persistent CTAs with a tile queue and cp.async
-prefetch, 2 TMA bulk tensor copies (lines up to 256 points)."""
+prefetch, 2 TMA bulk tensor copies (lines up to 256 points), 3 persistent
+CTAs with TMA copies double-buffered against the FFT work (lines up to 256
+points; 1-D grids fall back to another variant)."""
 import numpy as np
 import pytest
 
@@ -20,7 +22,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_variant_parity(monkeypatch, variant, case):
     require_gpu()
@@ -36,7 +38,7 @@ def test_variants_agree_bitwise_or_closely(monkeypatch):
     require_gpu()
     pr = synth.pyrazine_like(seed=8, n=(32, 32, 32))
     outs = []
-    for v in ("0", "1", "2"):
+    for v in ("0", "1", "2", "3"):
         monkeypatch.setenv("DSO_VARIANT", v)
         outs.append(gpu_propagate(pr, 4, "suzuki", 50.0, 25.0))
     for o in outs[1:]:
@@ -44,7 +46,7 @@ def test_variants_agree_bitwise_or_closely(monkeypatch):
         assert np.array_equal(o, outs[0])
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
 @pytest.mark.parametrize("n,S", [((16, 32, 8), 3), ((256,), 2)])
 def test_variant_parity_tvt(monkeypatch, variant, n, S):
     require_gpu()
