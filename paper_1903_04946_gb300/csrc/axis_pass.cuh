@@ -127,6 +127,88 @@ __device__ __forceinline__ void dft8(C* x) {
   x[7] = mkc(fma(-c, u3.x, e3.x), fma(-c, u3.y, e3.y));
 }
 
+// Twiddled radix-8 butterfly in tangent form.  A twiddle w = c + i s is
+// stored as (c, t) with t = s / c, so that w b = c (b + i t b): the rotation
+// b + i t b costs two FMAs, and both outputs a +- w b of a radix-2 pair then
+// cost two FMAs each, 6 FP64 instructions per pair instead of the 8 of a
+// complex multiply and two complex additions.  In a decimation-in-time
+// radix-8 stage the seven input twiddles are the powers w^r of one twiddle
+// w; splitting the 8-point DFT into three radix-2 layers and factoring the
+// common powers out of each pair leaves four distinct factors,
+//   w^4 (first layer), w^2 (second layer), w and W8 w (last layer),
+// with W8 = exp(-+ 2 pi i / 8) and the factors -+i of the other pairs free.
+// That is 12 pairs, 72 FP64 instructions per 8 points, against 7 complex
+// multiplies (28) plus the 52 of the butterfly.  A twiddle with c = 0 is
+// stored with c = 2^-500 (2^-60 in FP32) and t = s / c; the product c (b + i t b)
+// is then exact up to a relative error far below one ulp.
+template <bool INV, bool ROT, typename C>
+__device__ __forceinline__ void tan_pair(C& a, C& b, C w) {
+  // (a, b) <- (a + f b, a - f b), f = w (or conj w when INV), times -+i when ROT
+  const auto t = INV ? -w.y : w.y;
+  const auto c = w.x;
+  const auto zx = fma(-t, b.y, b.x);
+  const auto zy = fma(t, b.x, b.y);
+  C p, q;
+  if (!ROT) {
+    p = mkc(fma(c, zx, a.x), fma(c, zy, a.y));
+    q = mkc(fma(-c, zx, a.x), fma(-c, zy, a.y));
+  } else if (!INV) {  // -i (c z) = (c zy, -c zx)
+    p = mkc(fma(c, zy, a.x), fma(-c, zx, a.y));
+    q = mkc(fma(-c, zy, a.x), fma(c, zx, a.y));
+  } else {            // +i (c z) = (-c zy, c zx)
+    p = mkc(fma(-c, zy, a.x), fma(c, zx, a.y));
+    q = mkc(fma(c, zy, a.x), fma(-c, zx, a.y));
+  }
+  a = p;
+  b = q;
+}
+
+// 8-point DFT of (w^r x_r), r = 0..7, in place and in natural output order,
+// given the tangent-form factors w1 = w, w2 = w^2, w4 = w^4, w8 = W8 w.
+template <bool INV, typename C>
+__device__ __forceinline__ void dft8_tw(C* x, C w1, C w2, C w4, C w8) {
+  // first layer: pairs (r, r+4) with factor w^4
+  tan_pair<INV, false>(x[0], x[4], w4);
+  tan_pair<INV, false>(x[2], x[6], w4);
+  tan_pair<INV, false>(x[1], x[5], w4);
+  tan_pair<INV, false>(x[3], x[7], w4);
+  // second layer: 4-point DFTs of the even and odd halves, factor w^2
+  tan_pair<INV, false>(x[0], x[2], w2);
+  tan_pair<INV, true>(x[4], x[6], w2);
+  tan_pair<INV, false>(x[1], x[3], w2);
+  tan_pair<INV, true>(x[5], x[7], w2);
+  // now x0, x4, x2, x6 hold E_0..E_3 and x1, x5, x3, x7 hold O'_0..O'_3;
+  // last layer: y_k = E_k + W8^k w O'_k, y_{k+4} = E_k - W8^k w O'_k
+  tan_pair<INV, false>(x[0], x[1], w1);  // k = 0
+  tan_pair<INV, false>(x[4], x[5], w8);  // k = 1
+  tan_pair<INV, true>(x[2], x[3], w1);   // k = 2: W8^2 = -+i
+  tan_pair<INV, true>(x[6], x[7], w8);   // k = 3: W8^3 w = -+i W8 w
+  // outputs: y0 = x0, y4 = x1, y1 = x4, y5 = x5, y2 = x2, y6 = x3, y3 = x6, y7 = x7
+  const C y1 = x[4], y4 = x[1], y3 = x[6], y6 = x[3];
+  x[1] = y1;
+  x[4] = y4;
+  x[3] = y3;
+  x[6] = y6;
+}
+
+// Loads the four tangent-form factors of the butterfly with twiddle index
+// `step` (w = tw[step]) from a length-L tangent-form table, in global memory
+// (read-only path) or, with SHARED, in shared memory.
+template <int L, bool SHARED = false, typename C>
+__device__ __forceinline__ void load_tw8(const C* __restrict__ tw, int step, C& w1, C& w2, C& w4, C& w8) {
+  if constexpr (SHARED) {
+    w1 = tw[step];
+    w2 = tw[2 * step];
+    w4 = tw[4 * step];
+    w8 = tw[step + L / 8];
+  } else {
+    w1 = __ldg(&tw[step]);
+    w2 = __ldg(&tw[2 * step]);
+    w4 = __ldg(&tw[4 * step]);
+    w8 = __ldg(&tw[step + L / 8]);
+  }
+}
+
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void dftR(C* x) {
   if constexpr (R == 8) {
@@ -204,15 +286,13 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
         const int j = u * NB + beta;
         const int k = j & (Ls - 1);
         C* x = &v[s][beta * R];
-        if (Ls > 1) {
-          const int step = (L / (Ls * R)) * k;
-#pragma unroll
-          for (int r = 1; r < R; ++r) {
-            const C w = __ldg(&tw[r * step]);
-            x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
-          }
+        if (R == 8 && Ls > 1) {  // twiddled stages are radix 8 (the leftover radix goes first)
+          C w1, w2, w4, w8;
+          load_tw8<L>(tw, (L / (Ls * 8)) * k, w1, w2, w4, w8);
+          dft8_tw<INV>(x, w1, w2, w4, w8);
+        } else {
+          dftR<R, INV>(x);
         }
-        dftR<R, INV>(x);
         const int base = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) ln[base + r * Ls] = x[r];

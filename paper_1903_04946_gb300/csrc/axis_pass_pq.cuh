@@ -34,7 +34,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Stage with per-thread twiddles held in registers (used for the last stage
 // of 64-point lines, where each thread's k is fixed for the whole launch).
 template <int L, bool INV>
-__device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const double2 (&w)[8], int nslots, int tid,
+__device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const double2 (&w)[4], int nslots, int tid,
                                                 unsigned wmask) {
   constexpr int Q = L / 8;
   double2 v[8];
@@ -49,9 +49,7 @@ __device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const doubl
   stage_sync<L>(wmask);
   if (act) {
     const int k = u & (Ls - 1);
-#pragma unroll
-    for (int r = 1; r < 8; ++r) v[r] = INV ? cmulc(v[r], w[r]) : cmul(v[r], w[r]);
-    dftR<8, INV>(v);
+    dft8_tw<INV>(v, w[0], w[1], w[2], w[3]);
     const int base = (u - k) * 8 + k;
 #pragma unroll
     for (int r = 0; r < 8; ++r) ln[base + r * Ls] = v[r];
@@ -60,7 +58,7 @@ __device__ __forceinline__ void stockham8_regtw(double2* sm, int Ls, const doubl
 }
 
 template <int L, bool INV>
-__device__ __forceinline__ void fft_lines_pq(double2* sm, const double2* __restrict__ tw, const double2 (&wreg)[8],
+__device__ __forceinline__ void fft_lines_pq(double2* sm, const double2* __restrict__ tw, const double2 (&wreg)[4],
                                              int nslots, int tid, int nthr) {
   using PL = Plan<L>;
   const unsigned wmask = warp_lanes_mask(tid, nthr);
@@ -152,11 +150,10 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
   const int nslots = SV * G * (L / 8);
 
   // register twiddles for the second stage of 64-point lines
-  double2 wreg[8];
+  double2 wreg[4];
   if constexpr (L == 64) {
     const int k = (tid % (L / 8)) & 7;
-#pragma unroll
-    for (int r = 1; r < 8; ++r) wreg[r] = __ldg(&((const double2*)a.tw)[r * k]);
+    load_tw8<L>((const double2*)a.tw, k, wreg[0], wreg[1], wreg[2], wreg[3]);
   }
 
   __shared__ long long s_first;

@@ -108,15 +108,13 @@ __device__ __forceinline__ void tma_stage(double2* sm, int Ls, const double2* __
       const int j = u * NB + beta;
       const int k = j & (Ls - 1);
       double2* x = &v[beta * R];
-      if (Ls > 1) {
-        const int step = (L / (Ls * R)) * k;
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const double2 w = tws[r * step];
-          x[r] = INV ? cmulc(x[r], w) : cmul(x[r], w);
-        }
+      if (R == 8 && Ls > 1) {
+        double2 w1, w2, w4, w8;
+        load_tw8<L, true>(tws, (L / (Ls * 8)) * k, w1, w2, w4, w8);
+        dft8_tw<INV>(x, w1, w2, w4, w8);
+      } else {
+        dftR<R, INV>(x);
       }
-      dftR<R, INV>(x);
       const int base = (j - k) * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) ln[(base + r * Ls) << Wi_log2] = x[r];

@@ -380,7 +380,7 @@ dso_status ensure_twiddles(dso_ctx* c) {
   for (int d = 0; d < c->D; ++d) {
     const int l = ilog2(c->n[d]);
     if (c->tw[l]) continue;
-    std::vector<double2> h = host_twiddles((int)c->n[d]);
+    std::vector<double2> h = host_twiddles((int)c->n[d], c->prec == DSO_FP32);
     if (c->prec == DSO_FP32) {
       std::vector<float2> hf(h.size());
       for (size_t i = 0; i < h.size(); ++i) hf[i] = make_float2((float)h[i].x, (float)h[i].y);

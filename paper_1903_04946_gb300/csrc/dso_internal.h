@@ -52,9 +52,11 @@ cudaError_t launch_axis_pass_sv4(int L, int variant, const PassArgs& a, long lon
                                  const TmaMaps* maps, cudaStream_t st);
 
 // Operator tables (tables.cu).
-// Twiddles exp(-2 pi i m / L), m = 0..L-1, computed on the host in long
-// double and rounded once.
-std::vector<double2> host_twiddles(int L);
+// Twiddles w_m = exp(-2 pi i m / L), m = 0..L-1, in the tangent form the
+// FFT stages use: (cos, sin / cos), computed on the host in long double and
+// rounded once (a zero cosine is replaced by 2^-500, or 2^-60 for the FP32
+// table, so that the tangent stays finite).
+std::vector<double2> host_twiddles(int L, bool fp32);
 // Kinetic phase factors per axis: for each unique b (nb of them), the
 // D 1-D factor tables exp(-i b dt p_k^2 / (2 m_d)) concatenated over axes
 // (sum n_d entries), 1/P folded into axis 0.  Host long double.

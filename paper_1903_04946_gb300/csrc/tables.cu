@@ -4,7 +4,8 @@
 // operators U_V(a dt) and U_T(b dt) can be precomputed once for every unique
 // coefficient and stored; the index arrays I^a, I^b then say which one each
 // action uses.  This file builds
-//   * FFT twiddles exp(-2 pi i m / L), host long double;
+//   * FFT twiddles exp(-2 pi i m / L) in tangent form (cos, tan), host long
+//     double;
 //   * kinetic phases tau_b(p) = exp(-i b dt T(p)) / P with
 //     T(p) = sum_d p_d^2 / (2 m_d) (Eq. (diab_mol_ham)), as a product of 1-D
 //     factors computed on the host in long double (the 1/P of the unnormalised
@@ -19,12 +20,18 @@
 
 namespace dso {
 
-std::vector<double2> host_twiddles(int L) {
+std::vector<double2> host_twiddles(int L, bool fp32) {
   std::vector<double2> tw(L);
   const long double two_pi = 6.283185307179586476925286766559005768L;
+  // c = 0 (m = L/4) is stored as a tiny power of two: t = s / c stays finite
+  // and c (b + i t b) keeps the exact value to far below one ulp
+  const long double tiny = fp32 ? ldexpl(1.0L, -60) : ldexpl(1.0L, -500);
   for (int m = 0; m < L; ++m) {
     const long double ang = -two_pi * (long double)m / (long double)L;
-    tw[m] = make_double2((double)cosl(ang), (double)sinl(ang));
+    long double c = cosl(ang);
+    const long double sn = sinl(ang);
+    if (fabsl(c) < tiny) c = tiny;
+    tw[m] = make_double2((double)c, (double)(sn / c));
   }
   return tw;
 }
