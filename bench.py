@@ -220,6 +220,40 @@ def kind_name(k):
 # GPU arm
 # --------------------------------------------------------------------------
 
+def kernel_sources_hash() -> str:
+    """First 16 hex digits of the SHA-256 over the kernel headers (csrc/*.cuh,
+    csrc/*.h in name order, each prefixed by its base name)."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1903_04946_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*.h")),
+                    key=os.path.basename):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch (read + write) of `kernel` from the committed ncu
+    summaries, or None when no summary covers it or the kernel sources have
+    changed since the counters were taken."""
+    import glob
+    import re
+    want = kernel_sources_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            text = fh.read()
+        m = re.search(r"kernel_sources_sha256_16 = ([0-9a-f]{16})", text)
+        if not m or m.group(1) != want:
+            continue
+        for k, v in re.findall(r"traffic_bytes_per_launch: `(.+?)` = (\d+)", text):
+            if k == kernel:
+                return int(v), os.path.relpath(path, ROOT)
+    return None
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -255,6 +289,21 @@ def run_gpu(args):
     for _ in range(args.warmup):
         ctx.propagate(DT, DT)
     torch.cuda.synchronize()
+    if args.profile_steps:
+        # capture range for `ncu --profile-from-start off`: exactly these steps
+        l0 = dso.dso_launch_count(ctx.ctx)
+        torch.cuda.profiler.start()
+        with torch.cuda.stream(stream):
+            for _ in range(args.profile_steps):
+                ctx.propagate(DT, DT)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        launches = dso.dso_launch_count(ctx.ctx) - l0
+        ctx.close()
+        if rank == 0:
+            print(json.dumps({"profiled_steps": args.profile_steps, "workload": W.get("name", "pyrazine64"),
+                              "kernel_launches": int(launches)}))
+        return
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -331,6 +380,12 @@ def run_gpu(args):
                            "tflops": round(k["flops"] / (k["avg_ms"] * 1e-3) / 1e12, 4),
                            "gbs": round(k["bytes"] / (k["avg_ms"] * 1e-3) / 1e9, 1)} for k in kinds]})
     roofline["hbm_peak_gbs_measured"] = hbm_peak
+    tr = profiled_traffic(roofline["kernel"])
+    if tr is not None:
+        roofline["traffic"] = tr[0]
+        roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, {tr[1]}"
+    # the autotuned kernel configuration; DSO_PLAN=<this> reproduces it (profiling)
+    roofline["plan"] = dso.dso_tuned_plan(ctx.ctx)
 
     precision = None
     if fp32:
@@ -444,6 +499,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
     ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="after the warm-up, run this many steps inside cudaProfilerStart/Stop and exit "
+                         "(for ncu --profile-from-start off)")
     args = ap.parse_args()
     select_workload(args.workload, args.order or None)
     if args.warmup < 3:

@@ -166,6 +166,18 @@ dso_status dso_profile_steps(dso_ctx* ctx, double dt, int nsteps, int max_kinds,
  * blocking on any one of them. */
 int dso_busy(const dso_ctx* ctx);
 
+/* The kernel configuration the autotuner chose for this context, written to
+ * `out` (capacity `cap` bytes, NUL-terminated) as entries
+ * "axis,staged,variant,tile_lines,ctas_per_sm;" where staged is 0 for passes
+ * staging one surface and 1 for passes staging all S, and variant is 0 (one
+ * CTA per tile), 1 (persistent, cp.async), 2 (TMA) or 3 (persistent, TMA).
+ * Setting the environment variable DSO_PLAN to such a string before the
+ * first propagation makes a context use that configuration instead of timing
+ * the candidates (entries that do not fit the grid are ignored), so that a
+ * profiler run can reproduce the configuration of a timed run.  Returns the
+ * length written, or a negative dso_status (DSO_EINVAL if cap is too small). */
+int dso_tuned_plan(const dso_ctx* ctx, char* out, int cap);
+
 /* Number of kernel launches this context has issued since creation
  * (diagnostics: counts each launch of the library's own kernels, including
  * those inside CUDA-graph replays). */

@@ -26,7 +26,7 @@ EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
-    "dso_position_observables_noalloc", "dso_busy",
+    "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan",
 )
 
 _lib = None
@@ -65,6 +65,7 @@ def load(path: str = LIB):
         "dso_profile_steps": (i32, [vp, dbl, i32, i32, pi, pi, pi, pi, pi, pd, pi, pi]),
         "dso_launch_count": (i64, [vp]),
         "dso_busy": (i32, [vp]),
+        "dso_tuned_plan": (i32, [vp, ctypes.c_char_p, i32]),
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
     }
@@ -211,6 +212,15 @@ def dso_busy(ctx) -> bool:
     if r < 0:
         raise DSOError(r, "dso_busy")
     return r == 1
+
+
+def dso_tuned_plan(ctx) -> str:
+    """The autotuned kernel configuration, in the DSO_PLAN format."""
+    buf = ctypes.create_string_buffer(1024)
+    r = load().dso_tuned_plan(ctx, buf, 1024)
+    if r < 0:
+        raise DSOError(r, "dso_tuned_plan")
+    return buf.value.decode()
 
 
 def dso_launch_count(ctx) -> int:

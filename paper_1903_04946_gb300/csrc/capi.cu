@@ -458,6 +458,27 @@ TuneKey tune_key(const dso_ctx* c) {
 
 dso_status autotune_tiles(dso_ctx* c) {
   if (c->tuned) return DSO_OK;
+  // a fixed configuration (DSO_PLAN, as written by dso_tuned_plan)
+  if (const char* plan = getenv("DSO_PLAN")) {
+    const char* q = plan;
+    int d, w, v, g, cp, used;
+    while (sscanf(q, "%d,%d,%d,%d,%d;%n", &d, &w, &v, &g, &cp, &used) == 5) {
+      q += used;
+      if (d < 0 || d >= c->D || w < 0 || w > 1 || v < 0 || v > 3 || g < 1 || (g & (g - 1))) continue;
+      const long long L = c->n[d], lines = c->P / L;
+      const int SV = w ? c->S : 1;
+      if (g > axis_pass_max_tile_lines((int)L, SV) || lines % g) continue;
+      if (c->prec == DSO_FP32 && v != 0) continue;
+      if ((v == 1 && !axis_pass_pq_supported((int)L, SV, g)) || (v == 2 && !axis_pass_tma_supported((int)L, SV, g)) ||
+          (v == 3 && (!axis_pass_tmap_supported((int)L, SV, g) || c->D == 1)))
+        continue;
+      c->G[d][w] = g;
+      c->variant[d][w] = v;
+      c->cps[d][w] = cp < 0 ? 0 : cp;
+    }
+    c->tuned = true;
+    return DSO_OK;
+  }
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(tune_key(c));
@@ -540,7 +561,7 @@ dso_status autotune_tiles(dso_ctx* c) {
               continue;
             }
             if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-            for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_pass(c, p);
+            for (int r = 0; r < 10 && err == cudaSuccess; ++r) err = run_pass(c, p);
             if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
             if (err == cudaSuccess) err = cudaEventSynchronize(e1);
             float ms = 0.f;
@@ -554,7 +575,7 @@ dso_status autotune_tiles(dso_ctx* c) {
             const char* vb = getenv("DSO_TUNE_VERBOSE");
             if (vb && vb[0] == '1' && err == cudaSuccess)
               fprintf(stderr, "dso autotune: axis %d SV %d flags %d variant %d G %lld cps %d: %.2f us\n", d, SV,
-                      p.flags, var, G, c->cps[d][which], ms * 1000.f / 3.f);
+                      p.flags, var, G, c->cps[d][which], ms * 1000.f / 10.f);
           }
         }
       }
@@ -1069,6 +1090,20 @@ int dso_busy(const dso_ctx* c) {
 }
 
 int64_t dso_launch_count(const dso_ctx* c) { return c ? c->launches : 0; }
+
+int dso_tuned_plan(const dso_ctx* c, char* out, int cap) {
+  if (!c || !out || cap < 1) return fail(DSO_EINVAL, "dso_tuned_plan: null argument");
+  std::string s;
+  for (int d = 0; d < c->D; ++d)
+    for (int w = 0; w < 2; ++w) {
+      char e[64];
+      snprintf(e, sizeof(e), "%d,%d,%d,%d,%d;", d, w, c->variant[d][w], c->G[d][w], c->cps[d][w]);
+      s += e;
+    }
+  if ((int)s.size() + 1 > cap) return fail(DSO_EINVAL, "dso_tuned_plan: buffer too small");
+  std::memcpy(out, s.c_str(), s.size() + 1);
+  return (int)s.size();
+}
 
 const char* dso_last_error(void) { return g_err.c_str(); }
 

@@ -56,3 +56,31 @@ def test_variant_parity_tvt(monkeypatch, variant, n, S):
     ref = oracle_propagate(pr, 4, "suzuki", 2 * dt, dt, elementary="TVT")
     out = gpu_propagate(pr, 4, "suzuki", 2 * dt, dt, elementary="TVT")
     assert_parity(out, ref)
+
+
+def test_plan_round_trip(monkeypatch):
+    """The configuration the autotuner picks can be written out and forced
+    back (DSO_PLAN), giving the same kernels and the same bits."""
+    dso = require_gpu()
+    pr = synth.pyrazine_like(seed=9, n=(32, 16, 64))
+    ctx = dso.Context(pr, order=4, scheme=dso.DSO_SUZUKI)
+    ctx.propagate(80.0, 40.0)
+    plan = dso.dso_tuned_plan(ctx.ctx)
+    a = ctx.psi()
+    ctx.close()
+    assert plan.count(";") == 6
+    # a different configuration, forced: one CTA per tile, small tiles
+    monkeypatch.setenv("DSO_PLAN", "0,1,0,1,0;1,0,0,2,0;2,0,0,1,0;")
+    c2 = dso.Context(pr, order=4, scheme=dso.DSO_SUZUKI)
+    c2.propagate(80.0, 40.0)
+    assert dso.dso_tuned_plan(c2.ctx).startswith("0,0,")
+    assert "0,1,0,1,0;" in dso.dso_tuned_plan(c2.ctx)
+    b = c2.psi()
+    c2.close()
+    assert np.array_equal(a, b)
+    monkeypatch.setenv("DSO_PLAN", plan)
+    c3 = dso.Context(pr, order=4, scheme=dso.DSO_SUZUKI)
+    c3.propagate(80.0, 40.0)
+    assert dso.dso_tuned_plan(c3.ctx) == plan
+    assert np.array_equal(a, c3.psi())
+    c3.close()
