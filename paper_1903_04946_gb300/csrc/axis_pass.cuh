@@ -82,6 +82,16 @@ __device__ __forceinline__ C rot_i(C a) {
   return INV ? mkc(-a.y, a.x) : mkc(a.y, -a.x);
 }
 
+// Programmatic dependent launch.  Consecutive passes are launched so that a
+// pass's CTAs may become resident while the previous pass is still running
+// (its tail); `pdl_wait` blocks until the previous pass has completed and its
+// writes are visible, so it comes before any read of data that pass wrote.
+// `pdl_trigger` tells the scheduler that this CTA no longer needs the next
+// pass held back; once every CTA has triggered (or exited) the next pass
+// launches.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // In-place DFT of length 2, 4, 8 with sign -1 (forward) or +1 (INV).
 template <bool INV, typename C>
 __device__ __forceinline__ void dft2(C& a, C& b) {
@@ -517,6 +527,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   // line id lambda = o * stride + i; the tile covers lambdas [tile*G, tile*G+G)
   const TileGeom tg = make_geom(tj.tile, a);
 
+  pdl_wait();  // psi is the previous pass's output
   // load
   for (int s = 0; s < SV; ++s) {
     const C* src = psi + (size_t)(surf0 + s) * a.P;
@@ -529,6 +540,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
     }
   }
   __syncthreads();
+  pdl_trigger();
 
   const int nslots = SV * G * (L / 8);
   // The tile-wide steps (load, potential, kinetic phase, store) walk the tile

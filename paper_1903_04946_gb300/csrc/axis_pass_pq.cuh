@@ -157,6 +157,8 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
   }
 
   __shared__ long long s_first;
+  pdl_wait();  // psi and the queue reset are the previous pass's
+  pdl_trigger();
   if (tid == 0) s_first = (long long)atomicAdd(&queue[0], 1u);
   __syncthreads();
   long long cur = s_first;

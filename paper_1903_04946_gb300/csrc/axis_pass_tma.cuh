@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  pdl_wait();  // psi is the previous pass's output
   if (tid == 0) {
     // phase 0: tile and twiddles; phase 1: table for the first table step;
     // phase 2: kinetic table of a 1-D pass that also applies the potential
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
     }
     return;
   }
+  pdl_trigger();
 
   if (a.flags & PASS_INV_FIRST) {
     tma_fft<L, true>(x, tws, G, Wi_log2, nslots, tid, nthr);
@@ -402,6 +404,8 @@ __global__ void __launch_bounds__(256) axis_pass_tmap_kernel(PassArgs a, const _
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  pdl_wait();  // psi and the queue reset are the previous pass's
+  pdl_trigger();
   if (tid == 0) {
     mbar_expect_tx(&bar[2], (unsigned)(L * sizeof(double2)));
     bulk_load(tws, a.tw, (unsigned)(L * sizeof(double2)), &bar[2]);

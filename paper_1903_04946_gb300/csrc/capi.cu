@@ -127,6 +127,7 @@ struct dso_ctx {
   int G[DSO_MAX_DIM][2] = {};
   int variant[DSO_MAX_DIM][2] = {};
   int cps[DSO_MAX_DIM][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
+  int pdl = 0;               // programmatic dependent launch between passes (DSO_PDL=1: on)
   unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
   int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
@@ -254,6 +255,7 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.tau_elems = (long long)c->n_ttab * c->P;
   a.dec0 = c->dec0;
   a.ctas_per_sm = c->cps[p.axis][which];
+  a.pdl = c->pdl;
   const long long ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G)
                                           : (long long)c->B * c->S * (a.lines / a.G);
   const int variant = c->variant[p.axis][which];
@@ -657,6 +659,7 @@ dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_strea
   if (!c) return fail(DSO_ENOMEM, "host allocation failed");
   c->device = device;
   c->prec = precision;
+  if (const char* e = getenv("DSO_PDL")) c->pdl = (e[0] == '0') ? 0 : 1;
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {

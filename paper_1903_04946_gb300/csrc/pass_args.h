@@ -41,6 +41,7 @@ struct PassArgs {
   long long psi_elems, u_elems, tau_elems;
   int dec0;                // surface 0 uncoupled (block-diagonal potential): skip its zero products
   int ctas_per_sm;         // host side, persistent variants: resident CTAs per SM (0: as many as fit)
+  int pdl;                 // host side: launch with programmatic dependent launch
 };
 
 // Tile index -> (first staged surface over all jobs, job).  A pass staging

@@ -1,12 +1,35 @@
 // pass_launch.cuh -- per-(L, SV) instantiation and launch of axis_pass_kernel.
 #pragma once
 
+#include <utility>
+
 #include "axis_pass.cuh"
 #include "axis_pass_pq.cuh"
 #include "axis_pass_tma.cuh"
 #include "dso_internal.h"
 
 namespace dso {
+
+// Launch `k` on `st`; with `pdl`, as a programmatic dependent launch, so the
+// kernel's CTAs may start while the previous kernel on the stream finishes
+// (each axis-pass kernel waits for it with griddepcontrol.wait before its
+// first read of the wavefunction).  Inside stream capture this becomes a
+// programmatic edge of the CUDA graph.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, bool pdl,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 template <int L, int SV, typename C>
 cudaError_t launch_one_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
@@ -22,8 +45,8 @@ cudaError_t launch_one_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  axis_pass_kernel<L, SV, C><<<(unsigned)ntiles, threads, smem, st>>>(a);
-  return cudaGetLastError();
+  const cudaError_t e = launch_k(axis_pass_kernel<L, SV, C>, (unsigned)ntiles, threads, smem, st, a.pdl != 0, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int L, int SV>
@@ -61,8 +84,8 @@ cudaError_t launch_pq(const PassArgs& a, long long ntiles, unsigned* queue, cuda
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)per_sm * nsm[dev];
   if (grid > ntiles) grid = ntiles;
-  axis_pass_pq_kernel<L, SV><<<(unsigned)grid, threads, smem, st>>>(a, queue);
-  return cudaGetLastError();
+  e = launch_k(axis_pass_pq_kernel<L, SV>, (unsigned)grid, threads, smem, st, a.pdl != 0, a, queue);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int L, int SV>
@@ -79,8 +102,9 @@ cudaError_t launch_tma(const PassArgs& a, const TmaMaps* maps, long long ntiles,
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  axis_pass_tma_kernel<L, SV><<<(unsigned)ntiles, threads, smem, st>>>(a, *maps);
-  return cudaGetLastError();
+  const cudaError_t e = launch_k(axis_pass_tma_kernel<L, SV>, (unsigned)ntiles, threads, smem, st, a.pdl != 0, a,
+                                 *maps);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Persistent TMA variant: a grid of min(ntiles, CTAs per SM x SMs) CTAs
@@ -111,8 +135,8 @@ cudaError_t launch_tmap(const PassArgs& a, const TmaMaps* maps, long long ntiles
   if (a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm) per_sm = a.ctas_per_sm;
   long long grid = (long long)per_sm * nsm[dev];
   if (grid > ntiles) grid = ntiles;
-  axis_pass_tmap_kernel<L, SV><<<(unsigned)grid, threads, smem, st>>>(a, *maps, queue);
-  return cudaGetLastError();
+  e = launch_k(axis_pass_tmap_kernel<L, SV>, (unsigned)grid, threads, smem, st, a.pdl != 0, a, *maps, queue);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int L, int SV>

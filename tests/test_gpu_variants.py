@@ -84,3 +84,18 @@ def test_plan_round_trip(monkeypatch):
     assert dso.dso_tuned_plan(c3.ctx) == plan
     assert np.array_equal(a, c3.psi())
     c3.close()
+
+
+def test_programmatic_dependent_launch_changes_nothing(monkeypatch):
+    """Passes launched with programmatic dependent launch (the default) give
+    the same bits as plain stream-ordered launches (DSO_PDL=0)."""
+    dso = require_gpu()
+    pr = synth.pyrazine_like(seed=10, n=(32, 32, 32))
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DSO_PDL", flag)
+        for v in ("0", "2", "3"):
+            monkeypatch.setenv("DSO_VARIANT", v)
+            outs.append(gpu_propagate(pr, 6, "suzuki", 3 * 25.0, 25.0))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
