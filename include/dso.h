@@ -62,13 +62,14 @@ typedef enum {
 enum { DSO_HOST = 0, DSO_DEVICE = 1 };
 enum { DSO_FP64 = 0, DSO_FP32 = 1 };
 enum { DSO_TRIPLE_JUMP = 0, DSO_SUZUKI = 1 };
-enum { DSO_VTV = 0, DSO_TVT = 1 };
+enum { DSO_VTV = 0, DSO_TVT = 1, DSO_VT = 2, DSO_TV = 3 };
 
 /* Limits of this build. */
 #define DSO_MAX_DIM 3
 #define DSO_MAX_SURFACES 4
 #define DSO_MIN_AXIS 8
 #define DSO_MAX_AXIS 4096
+#define DSO_MAX_AXIS_1D 8192  /* a 1-D grid may be this long */
 
 /* Create a context on CUDA device `device`.  precision DSO_FP64 keeps psi,
  * the operator tables and the FFTs in FP64; DSO_FP32 stores psi and the
@@ -84,8 +85,12 @@ dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_strea
 void dso_destroy(dso_ctx* ctx);
 
 /* Grid of Sec. II G / App. B: D in 1..DSO_MAX_DIM axes, n[d] a power of two
- * in [DSO_MIN_AXIS, DSO_MAX_AXIS], qmax[d] > qmin[d] (host arrays of length
- * D).  Resets any loaded potential, masses, state and tables. */
+ * in [DSO_MIN_AXIS, DSO_MAX_AXIS] (a 1-D grid up to DSO_MAX_AXIS_1D),
+ * qmax[d] > qmin[d] (host arrays of length D).  Resets any loaded potential,
+ * masses, state and tables.  With S surfaces, a grid of D >= 2 needs
+ * S * n[0] <= 8192 (the potential pass holds all surfaces of an axis-0
+ * line); a 1-D grid longer than that runs its potential and kinetic steps
+ * as separate passes. */
 dso_status dso_set_grid(dso_ctx* ctx, int D, const int64_t* n, const double* qmin,
                         const double* qmax);
 
@@ -110,7 +115,14 @@ dso_status dso_load_potential(dso_ctx* ctx, int S, const double* V, int where);
  * and last, with the a~ coefficients) or DSO_TVT (Eq. (so_TVT): the kinetic
  * step acts first and last and takes the a~ coefficients, the potential the
  * b~); prune must be 1 (the coefficients of Eq.
- * (merging_splitting_coeff_b_zero)). */
+ * (merging_splitting_coeff_b_zero)).
+ * The first-order algorithms of Sec. II E take order 1 (scheme ignored):
+ * elementary DSO_VT (Eq. (so_VT): the kinetic step acts first, then the
+ * potential) or DSO_TV (Eq. (so_TV): the potential first).  They are not
+ * symmetric and are not composed; they serve as the paper's first-order
+ * reference (and negative control for the geometric properties).  They run
+ * on the VTV (TV) or TVT (VT) pass machinery with coefficients a = (1, 0),
+ * b = (1): the trailing zero-time action is the identity up to rounding. */
 dso_status dso_set_scheme(dso_ctx* ctx, int order, int scheme, int elementary, int prune);
 
 /* Set psi ([S][grid], complex128 or complex64 by the context's precision)

@@ -20,7 +20,7 @@ DSO_OK, DSO_EINVAL, DSO_ENOMEM, DSO_ECUDA, DSO_ESTATE, DSO_ETIMEOUT, DSO_ENUMERI
 DSO_HOST, DSO_DEVICE = 0, 1
 DSO_FP64, DSO_FP32 = 0, 1
 DSO_TRIPLE_JUMP, DSO_SUZUKI = 0, 1
-DSO_VTV, DSO_TVT = 0, 1
+DSO_VTV, DSO_TVT, DSO_VT, DSO_TV = 0, 1, 2, 3
 
 EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",

@@ -234,8 +234,9 @@ __device__ __forceinline__ void dftR(C* x) {
 // the leftover factor (2 or 4) as the first stage, whose twiddles are all 1.
 template <int L>
 struct Plan {
-  static constexpr int log2L = (L >= 4096) ? 12 : (L >= 2048) ? 11 : (L >= 1024) ? 10 : (L >= 512) ? 9
-                             : (L >= 256) ? 8 : (L >= 128) ? 7 : (L >= 64) ? 6 : (L >= 32) ? 5 : (L >= 16) ? 4 : 3;
+  static constexpr int log2L = (L >= 8192) ? 13 : (L >= 4096) ? 12 : (L >= 2048) ? 11 : (L >= 1024) ? 10
+                             : (L >= 512) ? 9 : (L >= 256) ? 8 : (L >= 128) ? 7 : (L >= 64) ? 6 : (L >= 32) ? 5
+                             : (L >= 16) ? 4 : 3;
   static constexpr int rem = log2L % 3;           // 0, 1 or 2 leftover binary stages
   static constexpr int first = rem == 0 ? 8 : (rem == 1 ? 2 : 4);
   static constexpr int n8 = log2L / 3 - (rem == 0 ? 1 : 0);  // radix-8 stages after the first

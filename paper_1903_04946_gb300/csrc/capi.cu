@@ -50,7 +50,15 @@ struct Pass {
   int flags;
   int u1 = -1, u2 = -1;  // potential table indices (first, second) or -1
   int tb = -1, tb2 = -1;  // kinetic table indices (first, second) or -1
+  int L = 0;              // line length of the pass's view of the grid (0: the axis length)
 };
+
+// Long 1-D grids (S * n > 8192): the potential step cannot hold all S
+// surfaces of the one line in shared memory, so it runs as its own pointwise
+// pass over the grid viewed as lines of kVLine points (any tiling of a
+// pointwise step is exact), and the FFTs and kinetic step as a pass with one
+// surface per line.
+constexpr int kVLine = 64;
 
 Pass mkpass(int axis, int SV, int flags, int u1 = -1, int u2 = -1, int tb = -1, int tb2 = -1) {
   Pass p;
@@ -114,7 +122,7 @@ struct dso_ctx {
   void* tau = nullptr;       // [nb][P] complex, context precision
   double* tau_a = nullptr;   // [na] potential coefficient * dt
   int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
-  void* tw[13] = {};         // per log2 L, context precision
+  void* tw[14] = {};         // per log2 L (L <= 8192), context precision
   // observables
   double* Tax = nullptr;     // per-axis p^2 / (2 m_d), concatenated
   void* work = nullptr;      // [S][P] complex, context precision
@@ -176,8 +184,14 @@ void drop_model(dso_ctx* c) {
 // CTA, so that many CTAs share each SM and the last wave is short.  A power
 // of two always divides the line count and either divides the axis stride or
 // is a multiple of it, which the tile geometry relies on.
-int choose_G(const dso_ctx* c, int axis, int SV) {
-  const int L = (int)c->n[axis];
+bool split_1d(const dso_ctx* c) { return c->D == 1 && (long long)c->S * c->n[0] > 8192; }
+
+// Line length of the passes of kind (axis d, staged surfaces 1 or S).
+int kind_L(const dso_ctx* c, int d, int which) {
+  return (d == 0 && which == 1 && split_1d(c)) ? kVLine : (int)c->n[d];
+}
+
+int choose_G(const dso_ctx* c, int L, int SV) {
   const long long lines = c->P / L;
   const long long target = (128LL * 8) / ((long long)SV * L);
   const long long gmax = axis_pass_max_tile_lines(L, SV);
@@ -219,7 +233,7 @@ bool encode_view(CUtensorMap* m, const void* base, long long P, int L, long long
 }
 
 cudaError_t run_pass(dso_ctx* c, const Pass& p) {
-  const int L = (int)c->n[p.axis];
+  const int L = p.L ? p.L : (int)c->n[p.axis];
   PassArgs a{};  // every field defined; the kernels read all of them
   const size_t es = c->esz();
   a.psi = c->psi;
@@ -231,6 +245,7 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
   a.tau2_scale = (double)c->P;
   a.tw = c->tw[ilog2(L)];
+  if (!a.tw) return cudaErrorInvalidValue;  // no twiddle table for this line length
   a.P = c->P;
   long long stride = 1;
   for (int d = p.axis + 1; d < c->D; ++d) stride *= c->n[d];
@@ -326,6 +341,13 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
         u1 = ia[last];
         u2 = ia[0];
       }
+      if (D == 1 && split_1d(c)) {
+        Pass v = mkpass(0, c->S, 0, u1, u2);
+        v.L = kVLine;
+        out.push_back(v);
+        out.push_back(mkpass(0, 1, PASS_FWD | PASS_T, -1, -1, ib[j]));
+        continue;
+      }
       if (D == 1) {
         out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, u1, u2, ib[j]));
         continue;
@@ -341,6 +363,15 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
     const int tb = (j == 0 && !first) ? ia[last] : ia[j];
     const int tb2 = (j == 0 && !first) ? ia[0] : -1;
     const int uv = (j == 0) ? (first ? -1 : ib[NB - 1]) : ib[j - 1];
+    if (D == 1 && split_1d(c)) {
+      if (uv >= 0) {
+        Pass v = mkpass(0, c->S, 0, uv);
+        v.L = kVLine;
+        out.push_back(v);
+      }
+      out.push_back(mkpass(0, 1, PASS_FWD | PASS_T, -1, -1, tb, tb2));
+      continue;
+    }
     if (D == 1) {
       out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, tb, tb2));
       continue;
@@ -356,10 +387,19 @@ std::vector<Pass> final_passes(const dso_ctx* c) {
   const int last = (int)c->coeffs.a.size() - 1;
   const int NB = (int)c->coeffs.b.size();
   if (c->elementary == DSO_VTV) {
-    out.push_back(mkpass(0, c->S, c->D == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last]));
+    Pass v = mkpass(0, c->S, c->D == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last]);
+    if (split_1d(c)) v.L = kVLine;
+    out.push_back(v);
     return out;
   }
   const int uv = c->coeffs.ib[NB - 1];
+  if (split_1d(c)) {
+    Pass v = mkpass(0, c->S, 0, uv);
+    v.L = kVLine;
+    out.push_back(v);
+    out.push_back(mkpass(0, 1, PASS_FWD | PASS_T, -1, -1, c->coeffs.ia[last]));
+    return out;
+  }
   if (c->D == 1) {
     out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, c->coeffs.ia[last]));
     return out;
@@ -379,10 +419,16 @@ std::vector<Pass> final_passes(const dso_ctx* c) {
   } while (0)
 
 dso_status ensure_twiddles(dso_ctx* c) {
-  for (int d = 0; d < c->D; ++d) {
-    const int l = ilog2(c->n[d]);
+  // every line length a pass uses: the axis lengths, and the view of the
+  // pointwise potential pass of a long 1-D grid (the persistent and TMA
+  // kernels stage the twiddles of their line length even when they do no FFT)
+  std::vector<int> lens;
+  for (int d = 0; d < c->D; ++d) lens.push_back((int)c->n[d]);
+  if (split_1d(c)) lens.push_back(kVLine);
+  for (int L : lens) {
+    const int l = ilog2(L);
     if (c->tw[l]) continue;
-    std::vector<double2> h = host_twiddles((int)c->n[d], c->prec == DSO_FP32);
+    std::vector<double2> h = host_twiddles(L, c->prec == DSO_FP32);
     if (c->prec == DSO_FP32) {
       std::vector<float2> hf(h.size());
       for (size_t i = 0; i < h.size(); ++i) hf[i] = make_float2((float)h[i].x, (float)h[i].y);
@@ -467,7 +513,7 @@ dso_status autotune_tiles(dso_ctx* c) {
     while (sscanf(q, "%d,%d,%d,%d,%d;%n", &d, &w, &v, &g, &cp, &used) == 5) {
       q += used;
       if (d < 0 || d >= c->D || w < 0 || w > 1 || v < 0 || v > 3 || g < 1 || (g & (g - 1))) continue;
-      const long long L = c->n[d], lines = c->P / L;
+      const long long L = kind_L(c, d, w), lines = c->P / L;
       const int SV = w ? c->S : 1;
       if (g > axis_pass_max_tile_lines((int)L, SV) || lines % g) continue;
       if (c->prec == DSO_FP32 && v != 0) continue;
@@ -529,7 +575,7 @@ dso_status autotune_tiles(dso_ctx* c) {
     p.tb2 = -1;
     const int d = p.axis, SV = p.SV, which = SV == 1 ? 0 : 1;
     {
-      const int L = (int)c->n[d];
+      const int L = kind_L(c, d, which);
       const long long lines = c->P / L;
       const int gmax = axis_pass_max_tile_lines(L, SV);
       bool any_whole = false;
@@ -689,8 +735,8 @@ dso_status dso_set_grid(dso_ctx* c, int D, const int64_t* n, const double* qmin,
   if (!c || !n || !qmin || !qmax) return fail(DSO_EINVAL, "null argument");
   if (D < 1 || D > DSO_MAX_DIM) return fail(DSO_EINVAL, "D must be 1..3");
   for (int d = 0; d < D; ++d) {
-    if (!is_pow2(n[d]) || n[d] < DSO_MIN_AXIS || n[d] > DSO_MAX_AXIS)
-      return fail(DSO_EINVAL, "each n[d] must be a power of two in [8, 4096]");
+    if (!is_pow2(n[d]) || n[d] < DSO_MIN_AXIS || n[d] > (D == 1 ? DSO_MAX_AXIS_1D : DSO_MAX_AXIS))
+      return fail(DSO_EINVAL, "each n[d] must be a power of two in [8, 4096] (a 1-D grid up to 8192)");
     if (!std::isfinite(qmin[d]) || !std::isfinite(qmax[d]) || !(qmax[d] > qmin[d]))
       return fail(DSO_EINVAL, "need finite qmin < qmax on every axis");
   }
@@ -741,9 +787,16 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   if (!c->have_grid) return fail(DSO_ESTATE, "grid not set");
   if (S < 2 || S > DSO_MAX_SURFACES) return fail(DSO_EINVAL, "S must be 2..4");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
-  for (int d = 0; d < c->D; ++d)
-    if (!axis_pass_supported((int)c->n[d], d == 0 ? S : 1) || (c->D == 1 && !axis_pass_supported((int)c->n[0], S)))
-      return fail(DSO_EINVAL, "axis length too long for this surface count (S * n[0] must be <= 8192)");
+  if (c->D == 1) {
+    // lines of S * n <= 8192 points fuse the potential with the FFT pass;
+    // longer ones (up to 8192 points per surface) run it as its own pass
+    if (!axis_pass_supported((int)c->n[0], 1))
+      return fail(DSO_EINVAL, "1-D grid too long (n must be <= 8192)");
+  } else {
+    for (int d = 0; d < c->D; ++d)
+      if (!axis_pass_supported((int)c->n[d], d == 0 ? S : 1))
+        return fail(DSO_EINVAL, "axis length too long for this surface count (S * n[0] must be <= 8192)");
+  }
   const size_t count = (size_t)c->B * (S * (S + 1) / 2) * c->P;
   if (where == DSO_HOST) {
     for (size_t i = 0; i < count; ++i)
@@ -790,8 +843,8 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   }
   CK(cudaStreamSynchronize(c->stream));
   for (int d = 0; d < c->D; ++d) {
-    c->G[d][0] = choose_G(c, d, 1);
-    c->G[d][1] = choose_G(c, d, S);
+    c->G[d][0] = choose_G(c, (int)c->n[d], 1);
+    c->G[d][1] = choose_G(c, (d == 0 && split_1d(c)) ? kVLine : (int)c->n[d], S);
     c->variant[d][0] = c->variant[d][1] = 0;
   }
   c->have_V = true;
@@ -800,9 +853,18 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
 
 dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int prune) {
   if (!c) return fail(DSO_EINVAL, "null context");
-  if (order < 2 || order > 10 || order % 2) return fail(DSO_EINVAL, "order must be 2, 4, 6, 8 or 10");
-  if (scheme != DSO_TRIPLE_JUMP && scheme != DSO_SUZUKI) return fail(DSO_EINVAL, "unknown scheme");
-  if (elementary != DSO_VTV && elementary != DSO_TVT) return fail(DSO_EINVAL, "elementary must be DSO_VTV or DSO_TVT");
+  const bool first_order = elementary == DSO_VT || elementary == DSO_TV;
+  if (first_order) {
+    if (order != 1) return fail(DSO_EINVAL, "DSO_VT and DSO_TV are first-order: order must be 1");
+    // TV (potential first) runs on the VTV machinery, VT (kinetic first) on TVT
+    elementary = (elementary == DSO_TV) ? DSO_VTV : DSO_TVT;
+    scheme = DSO_TRIPLE_JUMP;
+  } else {
+    if (order < 2 || order > 10 || order % 2) return fail(DSO_EINVAL, "order must be 2, 4, 6, 8 or 10");
+    if (scheme != DSO_TRIPLE_JUMP && scheme != DSO_SUZUKI) return fail(DSO_EINVAL, "unknown scheme");
+    if (elementary != DSO_VTV && elementary != DSO_TVT)
+      return fail(DSO_EINVAL, "elementary must be DSO_VTV, DSO_TVT, DSO_VT or DSO_TV");
+  }
   if (prune != 1) return fail(DSO_EINVAL, "only pruned coefficients are part of this build");
   try {
     Coeffs cf = build_coefficients(order, scheme);
@@ -1115,7 +1177,7 @@ const char* dso_last_error(void) { return g_err.c_str(); }
 namespace dso {
 
 bool axis_pass_supported(int L, int SV) {
-  if (L < 8 || L > 4096 || (L & (L - 1))) return false;
+  if (L < 8 || L > 8192 || (L & (L - 1))) return false;
   if (SV < 1 || SV > 4) return false;
   return (long long)SV * L <= 8192;
 }

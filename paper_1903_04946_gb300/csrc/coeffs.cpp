@@ -61,7 +61,17 @@ void find_unique(const std::vector<long double>& v, std::vector<double>& uniq, s
 }  // namespace
 
 Coeffs build_coefficients(int order, int scheme) {
-  if (order < 2 || order % 2 != 0 || order > 10) throw std::invalid_argument("order must be 2, 4, 6, 8 or 10");
+  if (order == 1) {  // first-order VT / TV (Sec. II E): a = (1, 0), b = (1)
+    Coeffs c;
+    c.a = {1.0, 0.0};
+    c.b = {1.0};
+    c.ia = {0, 1};
+    c.ib = {0};
+    c.a_unq = {1.0, 0.0};
+    c.b_unq = {1.0};
+    return c;
+  }
+  if (order < 2 || order % 2 != 0 || order > 10) throw std::invalid_argument("order must be 1, 2, 4, 6, 8 or 10");
   if (scheme != 0 && scheme != 1) throw std::invalid_argument("unknown composition scheme");
   std::vector<long double> g{1.0L};
   for (int p = 2; p < order; p += 2) {

@@ -176,6 +176,9 @@ cudaError_t launch_by_length(int L, int variant, const PassArgs& a, long long nt
     case 4096:
       if constexpr (SV * 4096 <= 8192) return launch_variant<4096, SV>(variant, a, ntiles, queue, maps, st);
       break;
+    case 8192:  // 1-D grids only, one surface per line
+      if constexpr (SV == 1) return launch_variant<8192, SV>(variant, a, ntiles, queue, maps, st);
+      break;
     default: break;
   }
   return cudaErrorInvalidValue;

@@ -154,7 +154,7 @@ def nai_like(seed: int = 1903, N: int = 1024, qmin: float = 3.0, qmax: float = 3
 # ---------------------------------------------------------------------------
 
 def pyrazine_like(seed: int = 1904, n=(64, 64, 64), S: int = 3, q_extent: float = 7.0,
-                  start_surface: int = 1) -> Problem:
+                  start_surface: int = 1, omega=None) -> Problem:
     """Seeded linear-plus-quadratic vibronic-coupling model in dimensionless
     normal coordinates.
 
@@ -168,10 +168,13 @@ def pyrazine_like(seed: int = 1904, n=(64, 64, 64), S: int = 3, q_extent: float 
     coupled by lambda q_c with lambda ~ U[0.005, 0.01] and q_c the last mode.
     The grid is [-q_extent, q_extent) on every axis.  psi0 is the ground
     vibrational state (sigma = 1, q0 = p0 = 0) placed on ``start_surface``.
+    ``omega`` fixes the frequencies (and so the masses) instead of drawing
+    them; the other draws are unchanged.
     """
     rng = np.random.default_rng(seed)
     D = len(n)
-    omega = rng.uniform(0.005, 0.02, size=D)
+    drawn = rng.uniform(0.005, 0.02, size=D)
+    omega = drawn if omega is None else np.asarray(omega, dtype=np.float64)
     E = np.zeros(S)
     if S > 1:
         E[1] = rng.uniform(0.12, 0.15)
@@ -318,3 +321,40 @@ def serving_job(seed: int, max_points: int = 1 << 21, min_points: int = 1 << 8):
     pr = Problem(n=n, qmin=qmin, qmax=qmax, mass=tuple(1.0 / omega), S=S, V=V, psi0=psi0,
                  name=f"serving_{seed}", params=dict(seed=seed, omega=omega))
     return pr, order, t, dt
+
+
+# ---------------------------------------------------------------------------
+# Mixed batch: many 1-D two-surface packets on uneven grids plus 3-D
+# three-surface instances on mixed 32/64 axes
+# ---------------------------------------------------------------------------
+
+BATCH_N_1D = (512, 1024, 2048, 4096, 8192)
+
+
+def batch_jobs(seed: int = 1905, n_1d: int = 512, n_3d: int = 32):
+    """Seeded mixed batch.  ``n_1d`` NaI-like packets with their own
+    potentials and initial states, N cycling through 512..8192 on the common
+    [3, 30) bohr range (mass 1.5e4); ``n_3d`` pyrazine-like instances whose
+    axes are each 32 or 64 points (the 8 shapes in turn), with seeded
+    couplings, vertical energies and shifts.  Instances of one shape share
+    their mode frequencies (drawn once per shape), hence their masses, so
+    that each shape advances as one batch.  Returns (jobs_1d, jobs_3d)."""
+    jobs_1d = [nai_like(seed=seed * 1000 + i, N=BATCH_N_1D[i % len(BATCH_N_1D)]) for i in range(n_1d)]
+    shapes = [(a, b, c) for a in (32, 64) for b in (32, 64) for c in (32, 64)]
+    rng = np.random.default_rng(seed)
+    omegas = {sh: rng.uniform(0.005, 0.02, size=3) for sh in shapes}
+    jobs_3d = []
+    for i in range(n_3d):
+        sh = shapes[i % len(shapes)]
+        jobs_3d.append(pyrazine_like(seed=seed * 1000 + 500 + i, n=sh, omega=omegas[sh]))
+    return jobs_1d, jobs_3d
+
+
+def group_batch(jobs):
+    """Group jobs that can share one batched context (same grid, masses and
+    surface count), keeping their order; returns a list of lists of indices."""
+    groups = {}
+    for i, pr in enumerate(jobs):
+        key = (tuple(pr.n), tuple(pr.qmin), tuple(pr.qmax), tuple(np.round(pr.mass, 12)), pr.S)
+        groups.setdefault(key, []).append(i)
+    return list(groups.values())

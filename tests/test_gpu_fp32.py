@@ -71,3 +71,16 @@ def test_fp32_rejects_fp64_only_variants(monkeypatch):
     ref = oracle_propagate(pr, 2, "triple_jump", 50.0, 25.0)
     out = gpu_propagate(pr, 2, "triple_jump", 50.0, 25.0, fp32=True)   # falls back to the tile kernel
     assert rel_l2(out.astype(np.complex128), ref) < 1e-5
+
+
+def test_fp32_precision_workload_full_size():
+    """The precision workload at its full size (128^3 x 3 surfaces, FP32
+    storage and FFTs), one triple-jump order-4 step against the FP64 oracle."""
+    require_gpu()
+    pr = synth.pyrazine_like(seed=1906, n=(128, 128, 128))
+    dt = 2000.0 / 128
+    ref = oracle_propagate(pr, 4, "triple_jump", dt, dt)
+    out = gpu_propagate(pr, 4, "triple_jump", dt, dt, fp32=True)
+    nfft = 2 * 3 * 3
+    err = rel_l2(out.astype(np.complex128), ref)
+    assert err <= _bound(nfft), (err, _bound(nfft))

@@ -154,9 +154,13 @@ def test_errors_are_reported(dso):
             dso.dso_set_psi(ctx, bad)
         assert ei.value.status == dso.DSO_ENUMERIC
         dso.dso_propagate(ctx, 0.0, 0.1)                   # zero steps: a no-op
-        dso.dso_set_grid(ctx, (4096,), (0.0,), (1.0,))
+        dso.dso_set_grid(ctx, (4096, 8), (0.0, 0.0), (1.0, 1.0))
         with pytest.raises(dso.DSOError):
-            dso.dso_load_potential(ctx, 3, np.zeros((6, 4096)))  # S * n > 8192
+            dso.dso_load_potential(ctx, 3, np.zeros((6, 4096, 8)))  # D >= 2 needs S * n[0] <= 8192
+        with pytest.raises(dso.DSOError):
+            dso.dso_set_grid(ctx, (16384,), (0.0,), (1.0,))        # 1-D grids up to 8192
+        with pytest.raises(dso.DSOError):
+            dso.dso_set_grid(ctx, (8192, 8), (0.0, 0.0), (1.0, 1.0))  # other axes up to 4096
     finally:
         dso.dso_destroy(ctx)
 
@@ -187,3 +191,13 @@ def test_tvt_time_reversible_and_norm(dso):
     ctx.close()
     assert abs(n1 - 1.0) < 1e-13
     assert rel_l2(back, pr.psi0) < 1e-12
+
+
+# -- long 1-D grids (S * n > 8192): the potential step runs as its own pass
+@pytest.mark.parametrize("N,S,el", [(8192, 2, "VTV"), (8192, 2, "TVT"), (4096, 3, "VTV"), (4096, 4, "TVT")])
+def test_long_1d_grids(dso, N, S, el):
+    pr = synth.nai_like(seed=31, N=N) if S == 2 else synth.random_coupled(N + S, (N,), S, extent=40.0)
+    dt = 1.0 if S == 2 else 0.2
+    ref = oracle_propagate(pr, 4, "suzuki", 3 * dt, dt, elementary=el)
+    out = gpu_propagate(pr, 4, "suzuki", 3 * dt, dt, elementary=el)
+    assert_parity(out, ref)

@@ -76,6 +76,18 @@ def test_library_coefficients_match_oracle(lib, scheme, order):
     assert list(ia) == list(sp.Ia) and list(ib) == list(sp.Ib)
 
 
+def test_library_first_order_coefficients(lib):
+    """Order 1 is the first-order VT / TV algorithm (Sec. II E): one action of
+    each operator with unit coefficient, written as a = (1, 0), b = (1) so
+    that the composed-step machinery runs it (the trailing action is the
+    zero-time identity)."""
+    a, b, ia, ib, nau, nbu = dso.dso_scheme_coefficients(1, dso.DSO_TRIPLE_JUMP)
+    assert list(a) == [1.0, 0.0] and list(b) == [1.0]
+    assert list(ia) == [0, 1] and list(ib) == [0] and (nau, nbu) == (2, 1)
+    oa, ob = C.first_order()
+    assert list(b) == ob and a[0] == oa[0]
+
+
 def test_library_rejects_bad_scheme(lib):
     with pytest.raises(dso.DSOError):
         dso.dso_scheme_coefficients(3, dso.DSO_TRIPLE_JUMP)
