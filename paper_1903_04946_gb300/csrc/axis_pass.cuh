@@ -260,12 +260,55 @@ __device__ __forceinline__ unsigned warp_lanes_mask(int tid, int nthr) {
   return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
 }
 
+// Shared-memory layout of the lines of a tile.  Element n of a line sits at
+// n + (n >> plog), one pad element after every 2^plog, and consecutive lines
+// are ls elements apart.  Unpadded, the Stockham stores of the early stages
+// (outputs Ls apart, Ls small) and the tile loads of strided axes (lines L
+// apart, L a multiple of the 32 banks) hit a few banks many times: 2.4-4.4x
+// the minimum number of shared-memory wavefronts, which in the FP32 mode made
+// the passes shared-memory bound (L1TEX 95 % busy, mio_throttle the top
+// stall).  The pad spacing (8 elements for 16-byte complex numbers, 16 for
+// 8-byte ones on lines of 128 or more) and the extra line offset X, chosen
+// with the tile's inner width Wi (Wi lines of consecutive addresses load
+// together), bring every stage and loop of the tile kernel to the minimum
+// (FP64, L >= 64) or within 1.14x of it (FP32, L >= 128), counted with a
+// model of the 32 banks over each warp-wide access.
+struct SmemLayout {
+  int ls;    // elements from one line to the next
+  int plog;  // log2 of the pad spacing (31: no padding)
+  __host__ __device__ __forceinline__ int pos(int n) const { return n + (n >> plog); }
+};
+
+__host__ __device__ inline SmemLayout tile_layout(int L, int esz, int Wi) {
+  SmemLayout s;
+  int X;
+  if (esz == 16) {
+    s.plog = 3;
+    X = (L >= 64) ? (Wi <= 8 ? 8 / Wi : 1) : 0;
+  } else if (L >= 128) {
+    s.plog = 4;
+    X = Wi <= 16 ? 16 / Wi : 1;
+  } else {
+    s.plog = 3;
+    X = 0;
+  }
+  s.ls = L + (L >> s.plog) + X;
+  return s;
+}
+
+__host__ __device__ inline SmemLayout plain_layout(int L) {
+  SmemLayout s;
+  s.ls = L;
+  s.plog = 31;
+  return s;
+}
+
 // One Stockham stage of radix R on every line of the tile held in `sm`.
 // Thread-slot s of this thread owns 8 consecutive butterfly inputs' worth of
 // work: 8/R butterflies j = u*(8/R) + beta of line `line`.
 template <int L, int R, bool INV, int K, typename C>
 __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restrict__ tw, int nslots, int tid,
-                                               int nthr, unsigned wmask) {
+                                               int nthr, unsigned wmask, const SmemLayout lay) {
   constexpr int NB = 8 / R;      // butterflies per slot
   constexpr int Q = L / R;       // butterflies per line
   C v[K][8];
@@ -275,12 +318,12 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
     if (gid < nslots) {
       const int line = gid / (L / 8);
       const int u = gid % (L / 8);
-      const C* ln = sm + (size_t)line * L;
+      const C* ln = sm + (size_t)line * lay.ls;
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[s][beta * R + r] = ln[j + r * Q];
+        for (int r = 0; r < R; ++r) v[s][beta * R + r] = ln[lay.pos(j + r * Q)];
       }
     }
   }
@@ -291,7 +334,7 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
     if (gid < nslots) {
       const int line = gid / (L / 8);
       const int u = gid % (L / 8);
-      C* ln = sm + (size_t)line * L;
+      C* ln = sm + (size_t)line * lay.ls;
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
@@ -306,7 +349,7 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
         }
         const int base = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) ln[base + r * Ls] = x[r];
+        for (int r = 0; r < R; ++r) ln[lay.pos(base + r * Ls)] = x[r];
       }
     }
   }
@@ -314,14 +357,15 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
 }
 
 template <int L, bool INV, int K, typename C>
-__device__ __forceinline__ void fft_lines(C* sm, const C* __restrict__ tw, int nslots, int tid, int nthr) {
+__device__ __forceinline__ void fft_lines(C* sm, const C* __restrict__ tw, int nslots, int tid, int nthr,
+                                          const SmemLayout lay) {
   using PL = Plan<L>;
   const unsigned wmask = warp_lanes_mask(tid, nthr);
-  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr, wmask);
+  stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr, wmask, lay);
   int Ls = PL::first;
 #pragma unroll 1
   for (int st = 0; st < PL::n8; ++st) {
-    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr, wmask);
+    stockham_stage<L, 8, INV, K>(sm, Ls, tw, nslots, tid, nthr, wmask, lay);
     Ls *= 8;
   }
 }
@@ -441,18 +485,19 @@ __device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], cons
 template <int L, int SV, typename C>
 __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, const TileGeom& tg, int G,
                                                 long long stride, long long P, int tid, int nthr,
-                                                const PassArgs* dbg = nullptr) {
+                                                const SmemLayout lay, const PassArgs* dbg = nullptr) {
   constexpr int NP = SV * (SV + 1) / 2;
   const int tile_pts = G * L;
+  const int tile_sz = G * lay.ls;  // shared-memory elements per staged surface
   const int dec0 = dbg ? dbg->dec0 : 0;
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
     const long long gi = tg.addr(g, n, L, stride);
-    const int off = g * L + n;
+    const int off = g * lay.ls + lay.pos(n);
     C x[SV], y[SV], u[NP];
 #pragma unroll
-    for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_pts + off];
+    for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_sz + off];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       if (SV > 2 && dec0 && k >= 1 && k < SV) {  // U_0c = 0: not loaded
@@ -472,7 +517,7 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
     }
     matvec_sym<SV>(u, x, y, dec0);
 #pragma unroll
-    for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_pts + off] = y[s];
+    for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_sz + off] = y[s];
   }
   __syncthreads();
 }
@@ -481,9 +526,10 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
 // one, whose 1/P factor belongs to an inverse FFT that does not run twice).
 template <int L, typename C>
 __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, const TileGeom& tg, int G, int SVl,
-                                              long long stride, int tid, int nthr, RealT<C> scale = 1,
-                                              const PassArgs* dbg = nullptr) {
+                                              long long stride, int tid, int nthr, RealT<C> scale,
+                                              const SmemLayout lay, const PassArgs* dbg = nullptr) {
   const int tile_pts = G * L;
+  const int tile_sz = G * lay.ls;
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
@@ -495,9 +541,9 @@ __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, 
 #endif
     C t = __ldg(&tau[tg.addr(g, n, L, stride)]);
     if (scale != (RealT<C>)1) t = cscale(t, scale);
-    const int off = g * L + n;
+    const int off = g * lay.ls + lay.pos(n);
     for (int s = 0; s < SVl; ++s) {
-      C* p = &sm[(size_t)s * tile_pts + off];
+      C* p = &sm[(size_t)s * tile_sz + off];
       *p = cmul(*p, t);
     }
   }
@@ -527,6 +573,8 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   const size_t uoff = (size_t)tj.job * a.u_batch_stride;
   // line id lambda = o * stride + i; the tile covers lambdas [tile*G, tile*G+G)
   const TileGeom tg = make_geom(tj.tile, a);
+  const SmemLayout lay = tile_layout(L, (int)sizeof(C), tg.Wi);
+  const int tile_sz = G * lay.ls;  // shared-memory elements per staged surface
 
   pdl_wait();  // psi is the previous pass's output
   // load
@@ -537,7 +585,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
       tile_elem<L>(e, tg, g, n);
       const long long gidx = (long long)(surf0 + s) * a.P + tg.addr(g, n, L, a.stride);
       if (DSO_CHECK_INDEX(gidx, a.psi_elems, 100, a.err))
-        sm[(size_t)s * tile_pts + g * L + n] = src[tg.addr(g, n, L, a.stride)];
+        sm[(size_t)s * tile_sz + g * lay.ls + lay.pos(n)] = src[tg.addr(g, n, L, a.stride)];
     }
   }
   __syncthreads();
@@ -548,23 +596,25 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   // in address order and end with a block barrier; the FFT stages in between
   // only synchronise the threads of each line.
   if (a.flags & PASS_INV_FIRST) {
-    fft_lines<L, true, K>(sm, tw, nslots, tid, nthr);
+    fft_lines<L, true, K>(sm, tw, nslots, tid, nthr, lay);
     __syncthreads();
   }
   if (SV > 1) {  // the host sets U1/U2 only for passes that stage all S surfaces
     if (a.U1)
-      apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U1) + uoff, tg, G, a.stride, a.P, tid, nthr, &a);
+      apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U1) + uoff, tg, G, a.stride, a.P, tid, nthr, lay,
+                             &a);
     if (a.U2)
-      apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U2) + uoff, tg, G, a.stride, a.P, tid, nthr, &a);
+      apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U2) + uoff, tg, G, a.stride, a.P, tid, nthr, lay,
+                             &a);
   }
-  if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, tw, nslots, tid, nthr);
+  if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, tw, nslots, tid, nthr, lay);
   if (a.flags & PASS_T) {
     __syncthreads();
-    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr, (RealT<C>)1, &a);
+    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr, (RealT<C>)1, lay, &a);
     if (a.tau2)
       apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau2), tg, G, SV, a.stride, tid, nthr,
-                       (RealT<C>)a.tau2_scale, &a);
-    fft_lines<L, true, K>(sm, tw, nslots, tid, nthr);
+                       (RealT<C>)a.tau2_scale, lay, &a);
+    fft_lines<L, true, K>(sm, tw, nslots, tid, nthr, lay);
   }
   __syncthreads();
 
@@ -580,7 +630,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
         DSO_RECORD(a.err, blockIdx.x, surf0, tg.o0, tg.i0, g, n, a.G, (a.stride_log2 << 16) | (tg.Wi_log2 << 8) | s);
 #endif
       if (DSO_CHECK_INDEX(gidx, a.psi_elems, 101, a.err))
-        dst[tg.addr(g, n, L, a.stride)] = sm[(size_t)s * tile_pts + g * L + n];
+        dst[tg.addr(g, n, L, a.stride)] = sm[(size_t)s * tile_sz + g * lay.ls + lay.pos(n)];
     }
   }
 }

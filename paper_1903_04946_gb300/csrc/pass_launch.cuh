@@ -37,8 +37,9 @@ cudaError_t launch_one_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const int threads = SV * a.G * (L / 8);
-  const size_t smem = (size_t)SV * a.G * L * sizeof(C);
-  if (threads > MaxThreads<L, SV>::value) return cudaErrorInvalidConfiguration;
+  const int Wi = 1 << (a.stride_log2 < a.G_log2 ? a.stride_log2 : a.G_log2);  // as make_geom
+  const size_t smem = (size_t)SV * a.G * tile_layout(L, (int)sizeof(C), Wi).ls * sizeof(C);
+  if (threads > MaxThreads<L, SV>::value || smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (!attr_set[dev]) {
     cudaError_t e = cudaFuncSetAttribute(axis_pass_kernel<L, SV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
