@@ -271,7 +271,7 @@ __device__ __forceinline__ unsigned warp_lanes_mask(int tid, int nthr) {
 // 8-byte ones on lines of 128 or more) and the extra line offset X, chosen
 // with the tile's inner width Wi (Wi lines of consecutive addresses load
 // together), bring every stage and loop of the tile kernel to the minimum
-// (FP64, L >= 64) or within 1.14x of it (FP32, L >= 128), counted with a
+// (FP64, L >= 64) or within 1.3x of it (FP32, L >= 128), counted with a
 // model of the 32 banks over each warp-wide access.
 struct SmemLayout {
   int ls;    // elements from one line to the next
