@@ -86,11 +86,11 @@ void dso_destroy(dso_ctx* ctx);
 
 /* Grid of Sec. II G / App. B: D in 1..DSO_MAX_DIM axes, n[d] a power of two
  * in [DSO_MIN_AXIS, DSO_MAX_AXIS] (a 1-D grid up to DSO_MAX_AXIS_1D),
- * at most 2^30 points in all, qmax[d] > qmin[d] (host arrays of length D).
- * Resets any loaded potential, masses, state and tables.  With S surfaces,
- * a grid of D >= 2 needs S * n[0] <= 8192 (the potential pass holds all
- * surfaces of an axis-0 line); a 1-D grid longer than that runs its
- * potential and kinetic steps as separate passes. */
+ * qmax[d] > qmin[d] (host arrays of length D).  Resets any loaded potential,
+ * masses, state and tables.  With S surfaces, a grid of D >= 2 needs
+ * S * n[0] <= 8192 (the potential pass holds all surfaces of an axis-0
+ * line); a 1-D grid longer than that runs its potential and kinetic steps
+ * as separate passes. */
 dso_status dso_set_grid(dso_ctx* ctx, int D, const int64_t* n, const double* qmin,
                         const double* qmax);
 

@@ -318,7 +318,7 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
     if (gid < nslots) {
       const int line = gid / (L / 8);
       const int u = gid % (L / 8);
-      const C* ln = sm + line * lay.ls;
+      const C* ln = sm + (size_t)line * lay.ls;
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
     if (gid < nslots) {
       const int line = gid / (L / 8);
       const int u = gid % (L / 8);
-      C* ln = sm + line * lay.ls;
+      C* ln = sm + (size_t)line * lay.ls;
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
@@ -379,10 +379,9 @@ struct TileGeom {
   int Wi;            // inner positions per outer row in the tile
   int Wi_log2;
   int stride_log2;
-  // 32-bit arithmetic: a surface holds fewer than 2^31 points (dso_set_grid)
-  __device__ __forceinline__ int addr(int g, int n, int L, long long /*stride*/) const {
-    const int o = (int)o0 + (g >> Wi_log2);
-    const int i = (int)i0 + (g & (Wi - 1));
+  __device__ __forceinline__ long long addr(int g, int n, long long L, long long /*stride*/) const {
+    const long long o = o0 + (g >> Wi_log2);
+    const long long i = i0 + (g & (Wi - 1));
     return ((o * L + n) << stride_log2) + i;
   }
 };
@@ -498,7 +497,7 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
     const int off = g * lay.ls + lay.pos(n);
     C x[SV], y[SV], u[NP];
 #pragma unroll
-    for (int s = 0; s < SV; ++s) x[s] = sm[s * tile_sz + off];
+    for (int s = 0; s < SV; ++s) x[s] = sm[(size_t)s * tile_sz + off];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       if (SV > 2 && dec0 && k >= 1 && k < SV) {  // U_0c = 0: not loaded
@@ -518,7 +517,7 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
     }
     matvec_sym<SV>(u, x, y, dec0);
 #pragma unroll
-    for (int s = 0; s < SV; ++s) sm[s * tile_sz + off] = y[s];
+    for (int s = 0; s < SV; ++s) sm[(size_t)s * tile_sz + off] = y[s];
   }
   __syncthreads();
 }
@@ -544,7 +543,7 @@ __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, 
     if (scale != (RealT<C>)1) t = cscale(t, scale);
     const int off = g * lay.ls + lay.pos(n);
     for (int s = 0; s < SVl; ++s) {
-      C* p = &sm[s * tile_sz + off];
+      C* p = &sm[(size_t)s * tile_sz + off];
       *p = cmul(*p, t);
     }
   }
@@ -586,7 +585,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
       tile_elem<L>(e, tg, g, n);
       const long long gidx = (long long)(surf0 + s) * a.P + tg.addr(g, n, L, a.stride);
       if (DSO_CHECK_INDEX(gidx, a.psi_elems, 100, a.err))
-        sm[s * tile_sz + g * lay.ls + lay.pos(n)] = src[tg.addr(g, n, L, a.stride)];
+        sm[(size_t)s * tile_sz + g * lay.ls + lay.pos(n)] = src[tg.addr(g, n, L, a.stride)];
     }
   }
   __syncthreads();
@@ -631,7 +630,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
         DSO_RECORD(a.err, blockIdx.x, surf0, tg.o0, tg.i0, g, n, a.G, (a.stride_log2 << 16) | (tg.Wi_log2 << 8) | s);
 #endif
       if (DSO_CHECK_INDEX(gidx, a.psi_elems, 101, a.err))
-        dst[tg.addr(g, n, L, a.stride)] = sm[s * tile_sz + g * lay.ls + lay.pos(n)];
+        dst[tg.addr(g, n, L, a.stride)] = sm[(size_t)s * tile_sz + g * lay.ls + lay.pos(n)];
     }
   }
 }

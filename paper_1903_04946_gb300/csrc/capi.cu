@@ -740,9 +740,6 @@ dso_status dso_set_grid(dso_ctx* c, int D, const int64_t* n, const double* qmin,
     if (!std::isfinite(qmin[d]) || !std::isfinite(qmax[d]) || !(qmax[d] > qmin[d]))
       return fail(DSO_EINVAL, "need finite qmin < qmax on every axis");
   }
-  long long pts = 1;
-  for (int d = 0; d < D; ++d) pts *= n[d];
-  if (pts > (1LL << 30)) return fail(DSO_EINVAL, "at most 2^30 grid points per surface");
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   drop_model(c);
