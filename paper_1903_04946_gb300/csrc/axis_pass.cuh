@@ -273,55 +273,44 @@ __device__ __forceinline__ unsigned warp_lanes_mask(int tid, int nthr) {
 // together), bring every stage and loop of the tile kernel to the minimum
 // (FP64, L >= 64) or within 1.3x of it (FP32, L >= 128), counted with a
 // model of the 32 banks over each warp-wide access.
-template <int PLOG>  // log2 of the pad spacing; 31: no padding
 struct SmemLayout {
-  int ls;  // elements from one line to the next
-  __host__ __device__ __forceinline__ int pos(int n) const { return n + (n >> PLOG); }
-  // offset of n + m from n when m is a multiple of the pad spacing
-  __host__ __device__ static constexpr int span(int m) { return PLOG >= 30 ? m : m + (m >> PLOG); }
+  int ls;    // elements from one line to the next
+  int plog;  // log2 of the pad spacing (31: no padding)
+  __host__ __device__ __forceinline__ int pos(int n) const { return n + (n >> plog); }
 };
 
-template <int L, typename C>
-__host__ __device__ constexpr int tile_plog() {
-  return sizeof(C) == 16 ? 3 : (L >= 128 ? 4 : 3);
-}
-
-template <int L, typename C>
-__host__ __device__ inline SmemLayout<tile_plog<L, C>()> tile_layout(int Wi) {
-  constexpr int P = tile_plog<L, C>();
+__host__ __device__ inline SmemLayout tile_layout(int L, int esz, int Wi) {
+  SmemLayout s;
   int X;
-  if (sizeof(C) == 16) {
+  if (esz == 16) {
+    s.plog = 3;
     X = (L >= 64) ? (Wi <= 8 ? 8 / Wi : 1) : 0;
   } else if (L >= 128) {
+    s.plog = 4;
     X = Wi <= 16 ? 16 / Wi : 1;
   } else {
+    s.plog = 3;
     X = 0;
   }
-  SmemLayout<P> s;
-  s.ls = L + (L >> P) + X;
+  s.ls = L + (L >> s.plog) + X;
   return s;
 }
 
-template <int L>
-__host__ __device__ inline SmemLayout<31> plain_layout() {
-  SmemLayout<31> s;
+__host__ __device__ inline SmemLayout plain_layout(int L) {
+  SmemLayout s;
   s.ls = L;
+  s.plog = 31;
   return s;
 }
 
 // One Stockham stage of radix R on every line of the tile held in `sm`.
 // Thread-slot s of this thread owns 8 consecutive butterfly inputs' worth of
 // work: 8/R butterflies j = u*(8/R) + beta of line `line`.
-// The reads at j + r Q and, when Ls is a multiple of the pad spacing, the
-// writes at base + r Ls are one padded base address plus r times a fixed
-// span, so the per-element index arithmetic folds into the access offsets.
-template <int L, int R, bool INV, int K, typename C, int PLOG>
+template <int L, int R, bool INV, int K, typename C>
 __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restrict__ tw, int nslots, int tid,
-                                               int nthr, unsigned wmask, const SmemLayout<PLOG> lay) {
+                                               int nthr, unsigned wmask, const SmemLayout lay) {
   constexpr int NB = 8 / R;      // butterflies per slot
   constexpr int Q = L / R;       // butterflies per line
-  constexpr bool qsep = PLOG >= 30 || (Q % (1 << (PLOG >= 30 ? 0 : PLOG))) == 0;
-  const bool lsep = PLOG >= 30 || (Ls & ((1 << (PLOG >= 30 ? 0 : PLOG)) - 1)) == 0;
   C v[K][8];
 #pragma unroll
   for (int s = 0; s < K; ++s) {
@@ -333,14 +322,8 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
 #pragma unroll
       for (int beta = 0; beta < NB; ++beta) {
         const int j = u * NB + beta;
-        if constexpr (qsep) {
-          const C* lp = ln + lay.pos(j);
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[s][beta * R + r] = lp[r * SmemLayout<PLOG>::span(Q)];
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[s][beta * R + r] = ln[lay.pos(j + r * Q)];
-        }
+        for (int r = 0; r < R; ++r) v[s][beta * R + r] = ln[lay.pos(j + r * Q)];
       }
     }
   }
@@ -365,24 +348,17 @@ __device__ __forceinline__ void stockham_stage(C* sm, int Ls, const C* __restric
           dftR<R, INV>(x);
         }
         const int base = (j - k) * R + k;
-        if (lsep) {
-          C* lp = ln + lay.pos(base);
-          const int step = SmemLayout<PLOG>::span(Ls);
 #pragma unroll
-          for (int r = 0; r < R; ++r) lp[r * step] = x[r];
-        } else {
-#pragma unroll
-          for (int r = 0; r < R; ++r) ln[lay.pos(base + r * Ls)] = x[r];
-        }
+        for (int r = 0; r < R; ++r) ln[lay.pos(base + r * Ls)] = x[r];
       }
     }
   }
   stage_sync<L>(wmask);
 }
 
-template <int L, bool INV, int K, typename C, int PLOG>
+template <int L, bool INV, int K, typename C>
 __device__ __forceinline__ void fft_lines(C* sm, const C* __restrict__ tw, int nslots, int tid, int nthr,
-                                          const SmemLayout<PLOG> lay) {
+                                          const SmemLayout lay) {
   using PL = Plan<L>;
   const unsigned wmask = warp_lanes_mask(tid, nthr);
   stockham_stage<L, PL::first, INV, K>(sm, 1, tw, nslots, tid, nthr, wmask, lay);
@@ -506,10 +482,10 @@ __device__ __forceinline__ void matvec_sym(const C (&u)[SV * (SV + 1) / 2], cons
 #define DSO_CHECK_INDEX(idx, extent, code, err) true
 #endif
 
-template <int L, int SV, typename C, int PLOG>
+template <int L, int SV, typename C>
 __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, const TileGeom& tg, int G,
                                                 long long stride, long long P, int tid, int nthr,
-                                                const SmemLayout<PLOG> lay, const PassArgs* dbg = nullptr) {
+                                                const SmemLayout lay, const PassArgs* dbg = nullptr) {
   constexpr int NP = SV * (SV + 1) / 2;
   const int tile_pts = G * L;
   const int tile_sz = G * lay.ls;  // shared-memory elements per staged surface
@@ -548,10 +524,10 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
 
 // `scale` multiplies the phase (1 for the first kinetic table; P for a second
 // one, whose 1/P factor belongs to an inverse FFT that does not run twice).
-template <int L, typename C, int PLOG>
+template <int L, typename C>
 __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, const TileGeom& tg, int G, int SVl,
                                               long long stride, int tid, int nthr, RealT<C> scale,
-                                              const SmemLayout<PLOG> lay, const PassArgs* dbg = nullptr) {
+                                              const SmemLayout lay, const PassArgs* dbg = nullptr) {
   const int tile_pts = G * L;
   const int tile_sz = G * lay.ls;
   for (int e = tid; e < tile_pts; e += nthr) {
@@ -597,7 +573,7 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   const size_t uoff = (size_t)tj.job * a.u_batch_stride;
   // line id lambda = o * stride + i; the tile covers lambdas [tile*G, tile*G+G)
   const TileGeom tg = make_geom(tj.tile, a);
-  const auto lay = tile_layout<L, C>(tg.Wi);
+  const SmemLayout lay = tile_layout(L, (int)sizeof(C), tg.Wi);
   const int tile_sz = G * lay.ls;  // shared-memory elements per staged surface
 
   pdl_wait();  // psi is the previous pass's output

@@ -63,14 +63,14 @@ __device__ __forceinline__ void fft_lines_pq(double2* sm, const double2* __restr
   using PL = Plan<L>;
   const unsigned wmask = warp_lanes_mask(tid, nthr);
   if constexpr (L == 64) {
-    stockham_stage<L, 8, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask, plain_layout<L>());
+    stockham_stage<L, 8, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask, plain_layout(L));
     stockham8_regtw<L, INV>(sm, 8, wreg, nslots, tid, wmask);
   } else {
-    stockham_stage<L, PL::first, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask, plain_layout<L>());
+    stockham_stage<L, PL::first, INV, 1>(sm, 1, tw, nslots, tid, nthr, wmask, plain_layout(L));
     int Ls = PL::first;
 #pragma unroll 1
     for (int st = 0; st < PL::n8; ++st) {
-      stockham_stage<L, 8, INV, 1>(sm, Ls, tw, nslots, tid, nthr, wmask, plain_layout<L>());
+      stockham_stage<L, 8, INV, 1>(sm, Ls, tw, nslots, tid, nthr, wmask, plain_layout(L));
       Ls *= 8;
     }
   }
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) axis_pass_pq_kernel(PassArgs a, unsigned*
       pq_potential<SV>(x, tb, tile_pts, tid, nthr, a.dec0);
       __syncthreads();
       if (a.U2) {
-        apply_potential<L, SV>(x, (const double2*)a.U2 + t.uoff, t.tg, G, a.stride, a.P, tid, nthr, plain_layout<L>(),
+        apply_potential<L, SV>(x, (const double2*)a.U2 + t.uoff, t.tg, G, a.stride, a.P, tid, nthr, plain_layout(L),
                                &a);
       }
       if (a.flags & PASS_T) {  // 1-D grids: the kinetic phase follows in this pass

@@ -38,7 +38,7 @@ cudaError_t launch_one_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const int threads = SV * a.G * (L / 8);
   const int Wi = 1 << (a.stride_log2 < a.G_log2 ? a.stride_log2 : a.G_log2);  // as make_geom
-  const size_t smem = (size_t)SV * a.G * tile_layout<L, C>(Wi).ls * sizeof(C);
+  const size_t smem = (size_t)SV * a.G * tile_layout(L, (int)sizeof(C), Wi).ls * sizeof(C);
   if (threads > MaxThreads<L, SV>::value || smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (!attr_set[dev]) {
     cudaError_t e = cudaFuncSetAttribute(axis_pass_kernel<L, SV, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
