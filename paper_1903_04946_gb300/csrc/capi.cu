@@ -28,6 +28,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/dso.h"
 #include "axis_pass_tma.cuh"
@@ -38,6 +39,16 @@ using namespace dso;
 namespace {
 
 thread_local std::string g_err = "no error";
+
+// NVTX range for the host-side extent of a library call (and the kernels it
+// enqueues), for profilers: `ncu --nvtx --nvtx-include "dso_propagate/"`
+// captures the kernels of propagations only.  Costs nothing without a tool.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 dso_status fail(dso_status s, const std::string& msg) {
   g_err = msg;
@@ -444,6 +455,7 @@ dso_status ensure_twiddles(dso_ctx* c) {
 
 dso_status ensure_tables(dso_ctx* c, double dt) {
   if (c->tables_valid && c->tables_dt == dt) return DSO_OK;
+  NvtxRange nvtx("dso_tables");
   CK(cudaGetLastError());  // surface any error left pending by an earlier call
   drop_tables(c);
   dso_status st = ensure_twiddles(c);
@@ -506,6 +518,7 @@ TuneKey tune_key(const dso_ctx* c) {
 
 dso_status autotune_tiles(dso_ctx* c) {
   if (c->tuned) return DSO_OK;
+  NvtxRange nvtx("dso_autotune");
   // a fixed configuration (DSO_PLAN, as written by dso_tuned_plan)
   if (const char* plan = getenv("DSO_PLAN")) {
     const char* q = plan;
@@ -909,6 +922,7 @@ dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {
 }
 
 dso_status dso_propagate(dso_ctx* c, double t, double dt) {
+  NvtxRange nvtx("dso_propagate");
   dso_status st = check_ready(c);
   if (st != DSO_OK) return st;
   if (!std::isfinite(t) || !std::isfinite(dt) || dt == 0.0) return fail(DSO_EINVAL, "t and dt must be finite, dt != 0");
@@ -988,6 +1002,7 @@ dso_status dso_get_psi(dso_ctx* c, void* out, int where) {
 }
 
 dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pops) {
+  NvtxRange nvtx("dso_observables");
   dso_status st = check_ready(c);
   if (st != DSO_OK) return st;
   DeviceGuard g(c->device);

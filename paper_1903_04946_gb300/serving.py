@@ -7,7 +7,12 @@ device-memory footprint fits the budget left by the jobs in flight, and
 advances every admitted job in chunks of time steps, each job on its own CUDA
 stream, so jobs admitted while others run overlap with them on the device.
 Finished jobs are read back, their latency (finish - arrival) recorded, and
-their memory returned to the budget for the next admission.
+their memory returned to the budget for the next admission.  A job can be
+cancelled at any time (`Server.cancel`): a waiting job is dropped, a running
+one is retired at its next chunk boundary without a result.  With a log
+path, every finished or cancelled job writes one JSON line: its shape, order,
+times, latency, and for finished jobs the norm, energy and populations of the
+result (FP64 reductions on the device).
 
 All propagation work runs in the library's kernels through the C ABI; this
 module only schedules.  Chunking a propagation does not change its result:
@@ -45,7 +50,9 @@ class Job:
     admitted: float = -1.0
     finished: float = -1.0
     footprint: int = 0
+    cancelled: bool = False
     result: np.ndarray = field(default=None, repr=False)
+    observables: tuple = field(default=None, repr=False)
 
     @property
     def substeps(self) -> int:
@@ -80,6 +87,12 @@ class Server:
         self.peak_used = 0
         self.chunk_steps = chunk_steps
         self.precision = precision
+        self._cancel = set()
+
+    def cancel(self, jid):
+        """Cancel job `jid`: dropped if waiting, retired without a result at
+        its next chunk boundary if running."""
+        self._cancel.add(jid)
 
     def _admit(self, job, now):
         job.ctx = Context(device=self.device, precision=self.precision)
@@ -89,15 +102,31 @@ class Server:
         self.used += job.footprint
         self.peak_used = max(self.peak_used, self.used)
 
-    def _retire(self, job, now):
-        job.result = job.ctx.psi()
+    def _retire(self, job, now, keep=True):
+        if keep:
+            job.result = job.ctx.psi()
+            job.observables = job.ctx.observables()
         job.ctx.close()
         job.ctx = None
         job.finished = now
         self.used -= job.footprint
 
-    def run(self, jobs):
-        """Serve `jobs` (arrival times in seconds from now); returns stats."""
+    @staticmethod
+    def _log_line(job):
+        rec = {"jid": job.jid, "D": job.problem.D, "n": list(job.problem.n), "S": job.problem.S,
+               "order": job.order, "steps": job.steps_total, "steps_done": job.steps_done,
+               "arrival_s": job.arrival, "admitted_s": job.admitted, "finished_s": job.finished,
+               "latency_s": job.finished - job.arrival if job.finished >= 0 else None,
+               "cancelled": job.cancelled}
+        if job.observables is not None:
+            norm, energy, pops = job.observables
+            rec.update(norm=float(norm), energy=float(energy), populations=[float(x) for x in pops])
+        return json.dumps(rec)
+
+    def run(self, jobs, log=None, on_tick=None):
+        """Serve `jobs` (arrival times in seconds from now); returns stats.
+        `log`: path of a JSON-lines file, one line per finished or cancelled
+        job.  `on_tick(server, now)`: called once per scheduling round."""
         for j in jobs:
             j.steps_total = int(round(j.t / j.dt))
             j.footprint = footprint_bytes(j.problem, j.order, j.scheme, 8 if self.precision else 16)
@@ -105,10 +134,18 @@ class Server:
                 raise ValueError(f"job {j.jid} needs {j.footprint} bytes, more than the budget")
         waiting = sorted(jobs, key=lambda j: j.arrival)
         active = []
+        logf = open(log, "w") if log else None
         t0 = time.perf_counter()
         max_active = 0
         while waiting or active:
             now = time.perf_counter() - t0
+            if on_tick is not None:
+                on_tick(self, now)
+            for job in [j for j in waiting if j.jid in self._cancel]:
+                waiting.remove(job)
+                job.cancelled = True
+                if logf:
+                    logf.write(self._log_line(job) + "\n")
             # admit arrived jobs in arrival order while their footprint fits
             while waiting and waiting[0].arrival <= now and self.used + waiting[0].footprint <= self.budget:
                 job = waiting.pop(0)
@@ -119,10 +156,20 @@ class Server:
             for job in list(active):
                 if dso_busy(job.ctx.ctx):
                     continue
+                if job.jid in self._cancel:
+                    job.cancelled = True
+                    self._retire(job, time.perf_counter() - t0, keep=False)
+                    active.remove(job)
+                    progressed = True
+                    if logf:
+                        logf.write(self._log_line(job) + "\n")
+                    continue
                 if job.steps_done >= job.steps_total:
                     self._retire(job, time.perf_counter() - t0)
                     active.remove(job)
                     progressed = True
+                    if logf:
+                        logf.write(self._log_line(job) + "\n")
                     continue
                 k = min(self.chunk_steps, job.steps_total - job.steps_done)
                 job.ctx.propagate(k * job.dt, job.dt)   # asynchronous on the job's stream
@@ -131,9 +178,13 @@ class Server:
             if not progressed:
                 time.sleep(0.0002)
         wall = time.perf_counter() - t0
-        lat = np.array([j.finished - j.arrival for j in jobs])
-        work = sum(j.problem.points * j.substeps * j.steps_total for j in jobs)
-        return {"jobs": len(jobs), "wall_seconds": wall, "p50_latency_s": float(np.percentile(lat, 50)),
+        if logf:
+            logf.close()
+        done = [j for j in jobs if not j.cancelled]
+        lat = np.array([j.finished - j.arrival for j in done]) if done else np.zeros(1)
+        work = sum(j.problem.points * j.substeps * j.steps_total for j in done)
+        return {"jobs": len(jobs), "cancelled": len(jobs) - len(done), "wall_seconds": wall,
+                "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
                 "throughput_grid_pts_substeps_per_s": work / wall, "max_concurrent_jobs": max_active,
                 "budget_bytes": self.budget, "peak_footprint_bytes": self.peak_used}
@@ -165,10 +216,11 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=0.0)
     ap.add_argument("--max-points", type=int, default=1 << 21)
     ap.add_argument("--seed", type=int, default=1907)
+    ap.add_argument("--log", default=None, help="JSON-lines file with one record per job")
     args = ap.parse_args()
     jobs = make_jobs(args.jobs, args.seed, args.load, args.max_points)
     srv = Server(budget_bytes=int(args.budget_gb * 2 ** 30) if args.budget_gb else None)
-    stats = srv.run(jobs)
+    stats = srv.run(jobs, log=args.log)
     stats.update(load=args.load, seed=args.seed, max_points=args.max_points,
                  workload="seeded Poisson stream: D in {1,2,3}, 2^8..2^21 points per surface, S in {2,3,4}, "
                           "orders 2-8 (triple jump), t in [500, 5000] a.u., complex128")

@@ -54,3 +54,36 @@ def test_admission_respects_budget():
         if j is not big:
             assert j.finished <= big.admitted or big.finished <= j.admitted, j.jid
     assert all(j.result is not None and np.all(np.isfinite(j.result)) for j in jobs)
+
+
+def test_cancellation_and_job_log(tmp_path):
+    """A waiting job cancelled before admission is dropped; a running job
+    cancelled mid-run is retired at its next chunk boundary without a result;
+    every other job finishes as if alone; the log has one line per job."""
+    require_gpu()
+    import json
+
+    from paper_1903_04946_gb300 import serving
+    jobs = serving.make_jobs(n_jobs=6, seed=11, load=8.0, max_points=1 << 12)
+    for j in jobs:
+        j.t = j.dt * min(int(round(j.t / j.dt)), 40)
+    srv = serving.Server(chunk_steps=2)
+    srv.cancel(jobs[5].jid)
+    target = jobs[0]
+
+    def tick(server, now):
+        if target.admitted >= 0 and target.steps_done > 0:
+            server.cancel(target.jid)
+
+    log = tmp_path / "jobs.jsonl"
+    stats = srv.run(jobs, log=str(log), on_tick=tick)
+    assert stats["cancelled"] == 2
+    recs = {r["jid"]: r for r in map(json.loads, log.read_text().splitlines())}
+    assert sorted(recs) == sorted(j.jid for j in jobs)
+    assert recs[jobs[5].jid]["cancelled"] and recs[jobs[5].jid]["admitted_s"] < 0
+    assert recs[target.jid]["cancelled"] and target.result is None
+    assert recs[target.jid]["steps_done"] < target.steps_total
+    for j in jobs[1:5]:
+        r = recs[j.jid]
+        assert not r["cancelled"] and abs(r["norm"] - 1.0) < 1e-10 and r["latency_s"] > 0
+        assert rel_l2(j.result, _alone(j)) <= 1e-12
