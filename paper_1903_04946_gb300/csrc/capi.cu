@@ -15,6 +15,7 @@
 //           next run in the same pass; final [I0 V(a~_{NB+1})].
 // All steps after the first have the same pass list, which is captured once
 // into a CUDA graph and replayed.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -54,6 +55,7 @@ dso_status fail(dso_status s, const std::string& msg) {
   g_err = msg;
   return s;
 }
+
 
 struct Pass {
   int axis;
@@ -896,27 +898,49 @@ dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int
   return DSO_OK;
 }
 
+// Finite check of a staged copy of psi on the device: a word whose exponent
+// bits are all ones (Inf or NaN) sets *flag.  n counts 8-byte words (FP64
+// components) or 4-byte words (FP32).
+__global__ void nonfinite_flag_kernel(const void* __restrict__ p, long long n, int fp32, int* flag) {
+  int bad = 0;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+  if (fp32) {
+    const unsigned* u = static_cast<const unsigned*>(p);
+    for (long long i = i0; i < n; i += step) bad |= (u[i] & 0x7f800000u) == 0x7f800000u;
+  } else {
+    const unsigned long long* u = static_cast<const unsigned long long*>(p);
+    for (long long i = i0; i < n; i += step) bad |= (u[i] & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {
   if (!c || !psi) return fail(DSO_EINVAL, "null argument");
   if (!c->have_V) return fail(DSO_ESTATE, "load the potential first (it fixes S)");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
   const size_t bytes = (size_t)c->B * c->S * c->P * c->esz();
-  if (where == DSO_HOST) {
-    const size_t n = 2 * (size_t)c->B * c->S * c->P;
-    if (c->prec == DSO_FP32) {
-      const float* p = (const float*)psi;
-      for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return fail(DSO_ENUMERIC, "psi has a non-finite value");
-    } else {
-      const double* p = (const double*)psi;
-      for (size_t i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return fail(DSO_ENUMERIC, "psi has a non-finite value");
-    }
-  }
   DeviceGuard g(c->device);
-  CK(cudaMemcpyAsync(c->psi, psi, bytes, where == DSO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                     c->stream));
-  if (where == DSO_HOST) CK(cudaStreamSynchronize(c->stream));
+  if (where == DSO_HOST) {
+    // Stage the host data in the work buffer, check it there (a few
+    // microseconds on the device instead of a pass over the host array), and
+    // only then copy it into psi, so a rejected input leaves psi unchanged.
+    if (!c->work) CK(cudaMalloc(&c->work, bytes));
+    int* flag = c->err + 15;
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+    CK(cudaMemcpyAsync(c->work, psi, bytes, cudaMemcpyHostToDevice, c->stream));
+    const long long words = 2LL * c->B * c->S * c->P;
+    const unsigned blocks = (unsigned)std::min<long long>((words + 255) / 256, 4096);
+    nonfinite_flag_kernel<<<blocks, 256, 0, c->stream>>>(c->work, words, c->prec == DSO_FP32 ? 1 : 0, flag);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    int hflag = 0;
+    CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hflag) return fail(DSO_ENUMERIC, "psi has a non-finite value");
+    CK(cudaMemcpyAsync(c->psi, c->work, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(c->psi, psi, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  }
   c->have_psi = true;
   return DSO_OK;
 }
@@ -990,14 +1014,11 @@ dso_status dso_get_psi(dso_ctx* c, void* out, int where) {
   if (!c->have_psi) return fail(DSO_ESTATE, "wavefunction not set");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
   DeviceGuard g(c->device);
-  if (where == DSO_HOST) {
-    dso_status fs = check_device_flag(c);
-    if (fs != DSO_OK) return fs;
-  }
   const size_t bytes = (size_t)c->B * c->S * c->P * c->esz();
   CK(cudaMemcpyAsync(out, c->psi, bytes, where == DSO_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                      c->stream));
-  if (where == DSO_HOST) CK(cudaStreamSynchronize(c->stream));
+  // the error flags come back after the copy, under the same synchronisation
+  if (where == DSO_HOST) return check_device_flag(c);
   return DSO_OK;
 }
 
