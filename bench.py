@@ -124,7 +124,10 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the raw samples go to DSO_BENCH_OUT (default: the system temporary directory)
+        import tempfile
+        out = os.environ.get("DSO_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_rank{device_index}.csv")
 
     def start(self):
         try:
