@@ -23,7 +23,8 @@ def _bound(nfft):
 @pytest.mark.parametrize("n,S,order,scheme,nsteps,el", [
     ((64, 64, 64), 3, 4, "triple_jump", 2, "VTV"), ((16, 32, 8), 3, 6, "suzuki", 1, "VTV"),
     ((32, 64), 4, 4, "suzuki", 2, "VTV"), ((1024,), 2, 2, "triple_jump", 20, "VTV"),
-    ((4096,), 2, 4, "triple_jump", 2, "VTV"), ((16, 32, 8), 3, 4, "suzuki", 2, "TVT")])
+    ((4096,), 2, 4, "triple_jump", 2, "VTV"), ((16, 32, 8), 3, 4, "suzuki", 2, "TVT"),
+    ((8192,), 2, 4, "suzuki", 2, "VTV")])
 def test_fp32_error_vs_fp64_oracle(n, S, order, scheme, nsteps, el):
     require_gpu()
     if len(n) == 3 and S == 3:
