@@ -8,3 +8,11 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
+
+
+def pytest_sessionstart(session):
+    # Host-only entry points of the library (coefficients, scheme digests,
+    # the serving loop's footprints) are used by CPU tests too: make sure the
+    # in-tree library exists (a no-op when it is up to date).
+    from paper_1903_04946_gb300.build import build
+    build()

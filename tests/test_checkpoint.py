@@ -10,6 +10,8 @@ from paper_1903_04946_gb300 import checkpoint
 
 
 def test_digest_names_the_composition():
+    dso.build()   # host-only entry point of the library (no GPU needed)
+    dso.load()
     d = checkpoint.scheme_digest(6, dso.DSO_SUZUKI, dso.DSO_VTV)
     assert d == checkpoint.scheme_digest(6, dso.DSO_SUZUKI, dso.DSO_VTV)
     others = {checkpoint.scheme_digest(6, dso.DSO_TRIPLE_JUMP, dso.DSO_VTV),
