@@ -243,8 +243,8 @@ def main():
     srv = Server(budget_bytes=int(args.budget_gb * 2 ** 30) if args.budget_gb else None)
     stats = srv.run(jobs, log=args.log)
     stats.update(load=args.load, seed=args.seed, max_points=args.max_points,
-                 workload="seeded Poisson stream: D in {1,2,3}, 2^8..2^21 points per surface, S in {2,3,4}, "
-                          "orders 2-8 (triple jump), t in [500, 5000] a.u., complex128")
+                 workload=f"seeded Poisson stream: D in {{1,2,3}}, 2^8..{args.max_points} points per surface, "
+                          "S in {2,3,4}, orders 2-8 (triple jump), t in [500, 5000] a.u., complex128")
     if args.sequential:
         secs, rate = run_sequential(make_jobs(args.jobs, args.seed, args.load, args.max_points))
         stats.update(sequential_seconds=secs, sequential_throughput_grid_pts_substeps_per_s=rate)
