@@ -125,6 +125,24 @@ dso_status dso_load_potential(dso_ctx* ctx, int S, const double* V, int where);
  * b = (1): the trailing zero-time action is the identity up to rounding. */
 dso_status dso_set_scheme(dso_ctx* ctx, int order, int scheme, int elementary, int prune);
 
+/* Any symmetric composition of the second-order step (Sec. II D): the
+ * m elementary coefficients gamma (host, time order) make one time step
+ * U(dt) = U_2(gamma_m dt) ... U_2(gamma_1 dt), with U_2 the elementary
+ * method DSO_VTV or DSO_TVT.  They are expanded, pruned and indexed as for
+ * the built-in schemes (Secs. II E-F).  This is how the paper's "optimal"
+ * compositions (Sec. II D, Table II), whose coefficients come from the
+ * literature and not from a recursion, are used.  Requirements: 1 <= m <=
+ * 4096, every gamma finite and nonzero, sum 1 within 1e-13, and
+ * gamma_k = gamma_{m+1-k} within 1e-14 of the largest; else DSO_EINVAL.
+ * The order of the result is whatever the coefficients achieve: the
+ * library does not check order conditions. */
+dso_status dso_set_composition(dso_ctx* ctx, int m, const double* gamma, int elementary);
+
+/* Host-only: the pruned coefficients that dso_set_composition would use,
+ * in the layout of dso_scheme_coefficients. */
+dso_status dso_composition_coefficients(int m, const double* gamma, int* n_a, int* n_b, double* a, double* b,
+                                        int* ia, int* ib, int* n_a_unq, int* n_b_unq);
+
 /* Set psi ([S][grid], complex128 or complex64 by the context's precision)
  * from host or device memory. */
 dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);

@@ -125,9 +125,12 @@ class Splitting:
     """Pruned splitting coefficients of one scheme/order, with unique-value
     tables; float64 views are exposed for the propagation."""
 
-    def __init__(self, order: int, scheme: str = TRIPLE_JUMP, pruned: bool = True):
+    def __init__(self, order: int, scheme: str = TRIPLE_JUMP, pruned: bool = True, gammas=None):
+        """With `gammas` (elementary-step coefficients of any symmetric
+        composition, time order) they replace the recursive TJ / Suzuki ones
+        and `order`, `scheme` are only labels."""
         self.order, self.scheme, self.pruned = order, scheme, pruned
-        self.gamma = composition(order, scheme)
+        self.gamma = composition(order, scheme) if gammas is None else [Decimal(float(g)) for g in gammas]
         self.a_full, self.b_full = expand(self.gamma)
         if pruned:
             self.a_dec, self.b_dec = prune(self.a_full, self.b_full)

@@ -22,13 +22,13 @@ VTV, TVT, VT, TV = "VTV", "TVT", "VT", "TV"
 
 
 def action_sequence(elementary: str = VTV, order: int = 2, scheme: str = C.TRIPLE_JUMP,
-                    pruned: bool = True):
+                    pruned: bool = True, gammas=None):
     """Ordered list of (operator, coefficient) for one time step; the first
     entry acts first."""
     if elementary in (VT, TV):
         A, B = ("T", "V") if elementary == VT else ("V", "T")
         return [(A, 1.0), (B, 1.0)]
-    sp = C.Splitting(order, scheme, pruned)
+    sp = C.Splitting(order, scheme, pruned, gammas=gammas)
     A, B = ("V", "T") if elementary == VTV else ("T", "V")
     seq = []
     for j in range(len(sp.b)):
@@ -86,12 +86,13 @@ class Propagator:
 
 
 def propagate(problem, t: float, dt: float, order: int = 2, scheme: str = C.TRIPLE_JUMP,
-              elementary: str = VTV, pruned: bool = True, psi=None):
+              elementary: str = VTV, pruned: bool = True, psi=None, gammas=None):
     """Propagate ``problem.psi0`` (or ``psi``) to time t with step dt;
-    t/dt must be an integer."""
+    t/dt must be an integer.  ``gammas``: explicit composition coefficients
+    in place of the recursive scheme."""
     nsteps = int(round(t / dt))
     if abs(nsteps * dt - t) > 1e-9 * max(1.0, abs(t)):
         raise ValueError("t must be an integer multiple of dt")
     prop = Propagator(problem)
-    seq = action_sequence(elementary, order, scheme, pruned)
+    seq = action_sequence(elementary, order, scheme, pruned, gammas)
     return prop.run(problem.psi0 if psi is None else psi, seq, dt, nsteps)

@@ -26,7 +26,8 @@ EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
-    "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan",
+    "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan", "dso_set_composition",
+    "dso_composition_coefficients",
 )
 
 _lib = None
@@ -66,6 +67,8 @@ def load(path: str = LIB):
         "dso_launch_count": (i64, [vp]),
         "dso_busy": (i32, [vp]),
         "dso_tuned_plan": (i32, [vp, ctypes.c_char_p, i32]),
+        "dso_set_composition": (i32, [vp, i32, pd, i32]),
+        "dso_composition_coefficients": (i32, [i32, pd, pi, pi, pd, pd, pi, pi, pi, pi]),
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
     }
@@ -212,6 +215,31 @@ def dso_busy(ctx) -> bool:
     if r < 0:
         raise DSOError(r, "dso_busy")
     return r == 1
+
+
+def dso_set_composition(ctx, gammas, elementary=DSO_VTV):
+    """Use the symmetric composition with elementary coefficients `gammas`."""
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    _check(load().dso_set_composition(ctx, int(g.size), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      elementary), "dso_set_composition")
+
+
+def dso_composition_coefficients(gammas):
+    """(a~, b~, I^a, I^b, N_a^unq, N_b^unq) of a user composition (host only)."""
+    lib = load()
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    gp = g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    na, nb, nau, nbu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.dso_composition_coefficients(int(g.size), gp, ctypes.byref(na), ctypes.byref(nb), None, None, None,
+                                            None, ctypes.byref(nau), ctypes.byref(nbu)),
+           "dso_composition_coefficients")
+    a = (ctypes.c_double * na.value)()
+    b = (ctypes.c_double * nb.value)()
+    ia = (ctypes.c_int * na.value)()
+    ib = (ctypes.c_int * nb.value)()
+    _check(lib.dso_composition_coefficients(int(g.size), gp, None, None, a, b, ia, ib, None, None),
+           "dso_composition_coefficients")
+    return (np.array(a[:]), np.array(b[:]), np.array(ia[:]), np.array(ib[:]), nau.value, nbu.value)
 
 
 def dso_tuned_plan(ctx) -> str:

@@ -898,6 +898,27 @@ dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int
   return DSO_OK;
 }
 
+// A user composition: 1..4096 finite nonzero elementary coefficients,
+// symmetric, summing to one.
+static dso_status check_gammas(int m, const double* gamma, std::vector<long double>& g) {
+  if (m < 1 || m > 4096 || !gamma) return fail(DSO_EINVAL, "need 1..4096 composition coefficients");
+  long double sum = 0.0L;
+  double big = 0.0;
+  g.assign(m, 0.0L);
+  for (int k = 0; k < m; ++k) {
+    if (!std::isfinite(gamma[k]) || gamma[k] == 0.0)
+      return fail(DSO_EINVAL, "composition coefficients must be finite and nonzero");
+    g[k] = gamma[k];
+    sum += g[k];
+    big = std::fmax(big, std::fabs(gamma[k]));
+  }
+  if (fabsl(sum - 1.0L) > 1e-13L) return fail(DSO_EINVAL, "composition coefficients must sum to 1");
+  for (int k = 0; k < m; ++k)
+    if (std::fabs(gamma[k] - gamma[m - 1 - k]) > 1e-14 * big)
+      return fail(DSO_EINVAL, "the composition must be symmetric (gamma_k = gamma_{m+1-k})");
+  return DSO_OK;
+}
+
 // Finite check of a staged copy of psi on the device: a word whose exponent
 // bits are all ones (Inf or NaN) sets *flag.  n counts 8-byte words (FP64
 // components) or 4-byte words (FP32).
@@ -912,6 +933,46 @@ __global__ void nonfinite_flag_kernel(const void* __restrict__ p, long long n, i
     for (long long i = i0; i < n; i += step) bad |= (u[i] & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+dso_status dso_set_composition(dso_ctx* c, int m, const double* gamma, int elementary) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (elementary != DSO_VTV && elementary != DSO_TVT) return fail(DSO_EINVAL, "elementary must be DSO_VTV or DSO_TVT");
+  std::vector<long double> g;
+  dso_status st = check_gammas(m, gamma, g);
+  if (st != DSO_OK) return st;
+  try {
+    Coeffs cf = coefficients_from_gammas(g);
+    DeviceGuard dg(c->device);
+    cudaStreamSynchronize(c->stream);
+    drop_tables(c);
+    c->coeffs = cf;
+    c->order = 0;  // a user composition
+    c->scheme = -1;
+    if (c->elementary != elementary) c->tuned = false;
+    c->elementary = elementary;
+    c->have_coeffs = true;
+  } catch (const std::exception& ex) {
+    return fail(DSO_EINVAL, ex.what());
+  }
+  return DSO_OK;
+}
+
+dso_status dso_composition_coefficients(int m, const double* gamma, int* n_a, int* n_b, double* a, double* b,
+                                        int* ia, int* ib, int* n_a_unq, int* n_b_unq) {
+  std::vector<long double> g;
+  dso_status st = check_gammas(m, gamma, g);
+  if (st != DSO_OK) return st;
+  Coeffs cf = coefficients_from_gammas(g);
+  if (n_a) *n_a = (int)cf.a.size();
+  if (n_b) *n_b = (int)cf.b.size();
+  if (n_a_unq) *n_a_unq = (int)cf.a_unq.size();
+  if (n_b_unq) *n_b_unq = (int)cf.b_unq.size();
+  if (a) std::memcpy(a, cf.a.data(), cf.a.size() * sizeof(double));
+  if (b) std::memcpy(b, cf.b.data(), cf.b.size() * sizeof(double));
+  if (ia) std::memcpy(ia, cf.ia.data(), cf.ia.size() * sizeof(int));
+  if (ib) std::memcpy(ib, cf.ib.data(), cf.ib.size() * sizeof(int));
+  return DSO_OK;
 }
 
 dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {

@@ -60,6 +60,29 @@ void find_unique(const std::vector<long double>& v, std::vector<double>& uniq, s
 
 }  // namespace
 
+Coeffs coefficients_from_gammas(const std::vector<long double>& g) {
+  // expand and prune in one scan: a's accumulate until a nonzero b closes them
+  std::vector<long double> at, bt;
+  long double pending = 0.0L;
+  bool open = false;
+  for (long double gam : g) {
+    const long double half = gam / 2.0L;
+    // first half-step V(gamma/2), kinetic T(gamma), second half-step V(gamma/2), kinetic T(0)
+    pending = open ? pending + half : half;
+    open = true;
+    at.push_back(pending);
+    bt.push_back(gam);
+    pending = half;  // opens the next accumulation; T(0) is pruned
+  }
+  at.push_back(pending);
+  Coeffs c;
+  for (long double x : at) c.a.push_back((double)x);
+  for (long double x : bt) c.b.push_back((double)x);
+  find_unique(at, c.a_unq, c.ia);
+  find_unique(bt, c.b_unq, c.ib);
+  return c;
+}
+
 Coeffs build_coefficients(int order, int scheme) {
   if (order == 1) {  // first-order VT / TV (Sec. II E): a = (1, 0), b = (1)
     Coeffs c;
@@ -82,26 +105,7 @@ Coeffs build_coefficients(int order, int scheme) {
       for (long double gi : g) next.push_back(go * gi);
     g.swap(next);
   }
-  // expand and prune in one scan: a's accumulate until a nonzero b closes them
-  std::vector<long double> at, bt;
-  long double pending = 0.0L;
-  bool open = false;
-  for (long double gam : g) {
-    const long double half = gam / 2.0L;
-    // first half-step V(gamma/2), kinetic T(gamma), second half-step V(gamma/2), kinetic T(0)
-    pending = open ? pending + half : half;
-    open = true;
-    at.push_back(pending);
-    bt.push_back(gam);
-    pending = half;  // opens the next accumulation; T(0) is pruned
-  }
-  at.push_back(pending);
-  Coeffs c;
-  for (long double x : at) c.a.push_back((double)x);
-  for (long double x : bt) c.b.push_back((double)x);
-  find_unique(at, c.a_unq, c.ia);
-  find_unique(bt, c.b_unq, c.ib);
-  return c;
+  return coefficients_from_gammas(g);
 }
 
 }  // namespace dso

@@ -24,6 +24,9 @@ struct Coeffs {
 
 // order in {2,4,...}, scheme 0 = triple jump, 1 = Suzuki fractal.
 Coeffs build_coefficients(int order, int scheme);
+// Pruned coefficients of the composition of second-order steps with the
+// elementary coefficients g (time order, symmetric).
+Coeffs coefficients_from_gammas(const std::vector<long double>& g);
 
 // Axis-pass launch: L = line length, SV = surfaces staged per tile.
 bool axis_pass_supported(int L, int SV);

@@ -107,3 +107,31 @@ def test_create_without_gpu_fails_cleanly(lib):
     st = lib.dso_create(ctypes.byref(ctx), 0, dso.DSO_FP64, None)
     assert st != dso.DSO_OK
     assert not ctx.value
+
+
+# a symmetric 7-stage composition that is not one of the recursive schemes
+CUSTOM7 = [0.21, -0.13, 0.37, 0.1, 0.37, -0.13, 0.21]
+
+
+def test_composition_coefficients_from_gammas(lib):
+    """dso_composition_coefficients expands any symmetric composition as the
+    built-in schemes are expanded: the triple-jump gammas give the order-4
+    triple-jump coefficients, and a custom composition matches the oracle's
+    expansion of the same gammas."""
+    x = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+    a, b, ia, ib, nau, nbu = dso.dso_composition_coefficients([x, 1.0 - 2.0 * x, x])
+    ra, rb, ria, rib, rnau, rnbu = dso.dso_scheme_coefficients(4, dso.DSO_TRIPLE_JUMP)
+    assert np.max(np.abs(a - ra)) < 1e-15 and np.max(np.abs(b - rb)) < 1e-15
+    assert list(ia) == list(ria) and list(ib) == list(rib) and (nau, nbu) == (rnau, rnbu)
+    g = np.array(CUSTOM7)
+    g[3] = 1.0 - (g.sum() - g[3])                      # sum exactly 1
+    a, b, ia, ib, nau, nbu = dso.dso_composition_coefficients(g)
+    sp = C.Splitting(0, C.TRIPLE_JUMP, gammas=g)
+    assert np.max(np.abs(a - np.array(sp.a))) <= 2e-16 and np.max(np.abs(b - np.array(sp.b))) <= 2e-16
+    assert list(ia) == list(sp.Ia) and list(ib) == list(sp.Ib)
+
+
+@pytest.mark.parametrize("bad", [[0.5, 0.6], [0.4, 0.2, 0.3], [0.5, 0.0, 0.5], [float("nan")], []])
+def test_composition_rejects_bad_gammas(lib, bad):
+    with pytest.raises(dso.DSOError):
+        dso.dso_composition_coefficients(bad)

@@ -121,3 +121,15 @@ def test_composition_length_and_bad_input():
         C.composition(3, C.SUZUKI)
     with pytest.raises(ValueError):
         C.composition(4, "optimal")
+
+
+@pytest.mark.parametrize("order,scheme", [(4, C.TRIPLE_JUMP), (6, C.SUZUKI), (8, C.TRIPLE_JUMP)])
+def test_explicit_gammas_reproduce_the_recursive_schemes(order, scheme):
+    """Splitting from explicit elementary-step coefficients (any symmetric
+    composition) equals the recursive construction when given its gammas
+    (rounded to double: the values agree to 1e-15)."""
+    ref = C.Splitting(order, scheme)
+    sp = C.Splitting(order, scheme, gammas=[float(g) for g in C.composition(order, scheme)])
+    assert len(sp.a) == len(ref.a) and len(sp.b) == len(ref.b)
+    assert max(abs(x - y) for x, y in zip(sp.a + sp.b, ref.a + ref.b)) < 1e-14
+    assert sp.Ia == ref.Ia and sp.Ib == ref.Ib
