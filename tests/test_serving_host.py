@@ -30,3 +30,78 @@ def test_footprint_grows_with_grid_order_and_surfaces():
     assert f(three, 4) > f(small, 4)
     P = 32 * 32
     assert f(small, 2) >= 2 * 2 * P * 16 + 3 * P * 8
+
+
+class _FakeContext:
+    """Stands in for a library context: records the steps it is asked to
+    propagate and reports itself busy for a few polls after each call."""
+    live = 0
+
+    def __init__(self, device=0, precision=0):
+        _FakeContext.live += 1
+        self.ctx = self
+        self.steps = 0
+        self.busy_polls = 0
+
+    def load_problem(self, pr):
+        self.pr = pr
+
+    def propagate(self, t, dt):
+        self.steps += int(round(t / dt))
+        self.busy_polls = 2
+
+    def psi(self):
+        return np.zeros((self.pr.S,) + tuple(self.pr.n), dtype=np.complex128)
+
+    def observables(self):
+        return 1.0, 0.5, np.array([1.0] + [0.0] * (self.pr.S - 1))
+
+    def close(self):
+        _FakeContext.live -= 1
+
+
+def _fake_busy(ctx):
+    if ctx.busy_polls > 0:
+        ctx.busy_polls -= 1
+        return True
+    return False
+
+
+def test_scheduler_admission_cancellation_and_log(monkeypatch, tmp_path):
+    """The serving loop's scheduling on the host: the admitted footprint never
+    exceeds the budget, every job gets exactly its steps in chunks, a
+    cancelled waiting job is never admitted, a job cancelled while running
+    stops early without a result, and the log has one line per job."""
+    import json
+
+    from paper_1903_04946_gb300 import serving
+    monkeypatch.setattr(serving, "Context", _FakeContext)
+    monkeypatch.setattr(serving, "dso_busy", _fake_busy)
+    monkeypatch.setattr(serving, "dso_set_scheme", lambda *a, **k: None)
+    jobs = serving.make_jobs(n_jobs=12, seed=21, load=50.0, max_points=1 << 12)
+    for j in jobs:
+        j.t = j.dt * min(int(round(j.t / j.dt)), 30)
+    fps = [serving.footprint_bytes(j.problem, j.order, j.scheme) for j in jobs]
+    budget = 3 * max(fps)
+    srv = serving.Server(budget_bytes=budget, chunk_steps=4)
+    srv.cancel(jobs[11].jid)
+    running = jobs[2]
+
+    def tick(server, now):
+        if running.steps_done >= 4:
+            server.cancel(running.jid)
+
+    log = tmp_path / "log.jsonl"
+    stats = srv.run(jobs, log=str(log), on_tick=tick)
+    assert stats["peak_footprint_bytes"] <= budget
+    assert stats["cancelled"] == 2 and _FakeContext.live == 0
+    recs = {r["jid"]: r for r in map(json.loads, log.read_text().splitlines())}
+    assert sorted(recs) == sorted(j.jid for j in jobs)
+    assert recs[jobs[11].jid]["admitted_s"] < 0 and recs[jobs[11].jid]["cancelled"]
+    assert recs[running.jid]["cancelled"] and running.result is None
+    assert 4 <= running.steps_done < running.steps_total
+    for j in jobs:
+        if j.cancelled:
+            continue
+        assert j.steps_done == j.steps_total and j.result is not None
+        assert recs[j.jid]["norm"] == 1.0 and recs[j.jid]["latency_s"] >= 0
