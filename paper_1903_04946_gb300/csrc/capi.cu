@@ -192,11 +192,7 @@ void drop_model(dso_ctx* c) {
   c->have_V = c->have_psi = false;
 }
 
-// Tile lines per surface for a pass along `axis` staging SV surfaces: the
-// largest power of two giving at most about 128 threads (8 values each) per
-// CTA, so that many CTAs share each SM and the last wave is short.  A power
-// of two always divides the line count and either divides the axis stride or
-// is a multiple of it, which the tile geometry relies on.
+// A 1-D grid whose S surfaces do not fit one line tile (see kVLine).
 bool split_1d(const dso_ctx* c) { return c->D == 1 && (long long)c->S * c->n[0] > 8192; }
 
 // Line length of the passes of kind (axis d, staged surfaces 1 or S).
@@ -204,6 +200,11 @@ int kind_L(const dso_ctx* c, int d, int which) {
   return (d == 0 && which == 1 && split_1d(c)) ? kVLine : (int)c->n[d];
 }
 
+// Tile lines per surface for a pass over lines of length L staging SV
+// surfaces: the largest power of two giving at most about 128 threads
+// (8 values each) per CTA, so that many CTAs share each SM and the last wave
+// is short.  A power of two always divides the line count and either divides
+// the axis stride or is a multiple of it, which the tile geometry relies on.
 int choose_G(const dso_ctx* c, int L, int SV) {
   const long long lines = c->P / L;
   const long long target = (128LL * 8) / ((long long)SV * L);
