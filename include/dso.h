@@ -143,6 +143,18 @@ dso_status dso_set_composition(dso_ctx* ctx, int m, const double* gamma, int ele
 dso_status dso_composition_coefficients(int m, const double* gamma, int* n_a, int* n_b, double* a, double* b,
                                         int* ia, int* ib, int* n_a_unq, int* n_b_unq);
 
+/* Norm monitor (failure detection).  Every split-operator step is unitary,
+ * so each job's norm may change only by round-off.  With tol > 0, every
+ * dso_propagate compares each job's norm after the call with the norm at
+ * the last dso_set_psi (or at the first checked call) and returns
+ * DSO_ENUMERIC, naming the job, when they differ by more than tol relative.
+ * This catches a corrupted state (non-finite values, a faulty input, a
+ * hardware or software error) at the call where it appears.  A checked
+ * dso_propagate synchronises its stream (one reduction of psi and a copy of
+ * B numbers).  tol = 0 (the default) switches the check off; tol < 0 or
+ * non-finite is DSO_EINVAL.  The paper has no counterpart. */
+dso_status dso_set_norm_check(dso_ctx* ctx, double tol);
+
 /* Set psi ([S][grid], complex128 or complex64 by the context's precision)
  * from host or device memory. */
 dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);

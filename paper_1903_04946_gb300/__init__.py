@@ -27,7 +27,7 @@ EXPORTS = (
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
     "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan", "dso_set_composition",
-    "dso_composition_coefficients",
+    "dso_composition_coefficients", "dso_set_norm_check",
 )
 
 _lib = None
@@ -68,6 +68,7 @@ def load(path: str = LIB):
         "dso_busy": (i32, [vp]),
         "dso_tuned_plan": (i32, [vp, ctypes.c_char_p, i32]),
         "dso_set_composition": (i32, [vp, i32, pd, i32]),
+        "dso_set_norm_check": (i32, [vp, dbl]),
         "dso_composition_coefficients": (i32, [i32, pd, pi, pi, pd, pd, pi, pi, pi, pi]),
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
@@ -222,6 +223,12 @@ def dso_set_composition(ctx, gammas, elementary=DSO_VTV):
     g = np.ascontiguousarray(gammas, dtype=np.float64)
     _check(load().dso_set_composition(ctx, int(g.size), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       elementary), "dso_set_composition")
+
+
+def dso_set_norm_check(ctx, tol):
+    """Fail dso_propagate (DSO_ENUMERIC) when a job's norm drifts by more
+    than `tol` relative; 0 switches the check off."""
+    _check(load().dso_set_norm_check(ctx, float(tol)), "dso_set_norm_check")
 
 
 def dso_composition_coefficients(gammas):

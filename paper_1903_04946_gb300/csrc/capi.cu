@@ -141,6 +141,11 @@ struct dso_ctx {
   void* work = nullptr;      // [S][P] complex, context precision
   double* partials = nullptr;
   double* obs_out = nullptr;
+  // norm monitor (dso_set_norm_check): tolerance (0: off), per-job norms at
+  // the last dso_set_psi, device partial sums
+  double norm_tol = 0.0;
+  std::vector<double> norm_ref;
+  double* norm_part = nullptr;
   // graph of one middle time step
   cudaGraphExec_t step_exec = nullptr;
   int step_exec_passes = 0;
@@ -189,6 +194,8 @@ void drop_model(dso_ctx* c) {
   dfree(c->work);
   dfree(c->partials);
   dfree(c->obs_out);
+  dfree(c->norm_part);
+  c->norm_ref.clear();
   c->have_V = c->have_psi = false;
 }
 
@@ -899,6 +906,54 @@ dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int
   return DSO_OK;
 }
 
+// Per-job squared norms sum |psi|^2 (no grid measure): block k of job b
+// writes the sum of its grid-stride share to part[b * kNormBlocks + k]; the
+// host adds the kNormBlocks values of a job in order, so the result is the
+// same on every run.
+constexpr int kNormBlocks = 64;
+__global__ void norm_partial_kernel(const void* __restrict__ psi, long long per_job, int fp32, double* part) {
+  __shared__ double red[256];
+  const int b = blockIdx.y;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_job;
+       i += (long long)gridDim.x * blockDim.x) {
+    double re, im;
+    if (fp32) {
+      const float2 v = static_cast<const float2*>(psi)[b * per_job + i];
+      re = v.x;
+      im = v.y;
+    } else {
+      const double2 v = static_cast<const double2*>(psi)[b * per_job + i];
+      re = v.x;
+      im = v.y;
+    }
+    acc = fma(re, re, fma(im, im, acc));
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[b * kNormBlocks + blockIdx.x] = red[0];
+}
+
+// Squared norms of every job's psi (synchronises the stream).
+static dso_status job_norms(dso_ctx* c, std::vector<double>& out) {
+  if (!c->norm_part) CK(cudaMalloc(&c->norm_part, (size_t)c->B * kNormBlocks * sizeof(double)));
+  norm_partial_kernel<<<dim3(kNormBlocks, c->B), 256, 0, c->stream>>>(c->psi, (long long)c->S * c->P,
+                                                                       c->prec == DSO_FP32 ? 1 : 0, c->norm_part);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  std::vector<double> h((size_t)c->B * kNormBlocks);
+  CK(cudaMemcpyAsync(h.data(), c->norm_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  out.assign(c->B, 0.0);
+  for (int b = 0; b < c->B; ++b)
+    for (int k = 0; k < kNormBlocks; ++k) out[b] += h[(size_t)b * kNormBlocks + k];
+  return DSO_OK;
+}
+
 // A user composition: 1..4096 finite nonzero elementary coefficients,
 // symmetric, summing to one.
 static dso_status check_gammas(int m, const double* gamma, std::vector<long double>& g) {
@@ -959,6 +1014,14 @@ dso_status dso_set_composition(dso_ctx* c, int m, const double* gamma, int eleme
   return DSO_OK;
 }
 
+dso_status dso_set_norm_check(dso_ctx* c, double tol) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (!std::isfinite(tol) || tol < 0.0) return fail(DSO_EINVAL, "tol must be finite and >= 0");
+  c->norm_tol = tol;
+  c->norm_ref.clear();  // taken again from the current psi at the next check
+  return DSO_OK;
+}
+
 dso_status dso_composition_coefficients(int m, const double* gamma, int* n_a, int* n_b, double* a, double* b,
                                         int* ia, int* ib, int* n_a_unq, int* n_b_unq) {
   std::vector<long double> g;
@@ -1004,6 +1067,7 @@ dso_status dso_set_psi(dso_ctx* c, const void* psi, int where) {
     CK(cudaMemcpyAsync(c->psi, psi, bytes, cudaMemcpyDeviceToDevice, c->stream));
   }
   c->have_psi = true;
+  c->norm_ref.clear();  // a new state: the norm monitor takes its reference again
   return DSO_OK;
 }
 
@@ -1029,6 +1093,10 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
       st = autotune_tiles(c);
       if (st != DSO_OK) return st;
     }
+    if (c->norm_tol > 0.0 && c->norm_ref.empty()) {
+      st = job_norms(c, c->norm_ref);
+      if (st != DSO_OK) return st;
+    }
     for (const Pass& p : step_passes(c, true)) CK(run_pass(c, p));
     if (nsteps > 1) {
       const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy && c->stream != cudaStreamPerThread;
@@ -1046,6 +1114,17 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
       }
     }
     for (const Pass& p : final_passes(c)) CK(run_pass(c, p));
+    if (c->norm_tol > 0.0) {  // the propagation is unitary: the norm may move by round-off only
+      std::vector<double> now;
+      st = job_norms(c, now);
+      if (st != DSO_OK) return st;
+      for (int b = 0; b < c->B; ++b) {
+        const double ref = c->norm_ref[b], drift = std::fabs(std::sqrt(now[b]) - std::sqrt(ref));
+        if (!(drift <= c->norm_tol * std::sqrt(ref)))
+          return fail(DSO_ENUMERIC, "norm of job " + std::to_string(b) + " drifted by " + std::to_string(drift) +
+                                        " (relative tolerance " + std::to_string(c->norm_tol) + ")");
+      }
+    }
   } catch (const std::exception& ex) {
     return fail(DSO_EINVAL, ex.what());
   }
