@@ -224,13 +224,14 @@ def kind_name(k):
 # --------------------------------------------------------------------------
 
 def kernel_sources_hash() -> str:
-    """First 16 hex digits of the SHA-256 over the kernel headers (csrc/*.cuh,
-    csrc/*.h in name order, each prefixed by its base name)."""
+    """First 16 hex digits of the SHA-256 over the device code of the axis
+    passes (csrc/*.cuh and their argument struct csrc/pass_args.h, in name
+    order, each prefixed by its base name)."""
     import glob
     import hashlib
     csrc = os.path.join(ROOT, "paper_1903_04946_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + glob.glob(os.path.join(csrc, "*.h")),
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + [os.path.join(csrc, "pass_args.h")],
                     key=os.path.basename):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
