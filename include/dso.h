@@ -155,8 +155,11 @@ dso_status dso_composition_coefficients(int m, const double* gamma, int* n_a, in
  * non-finite is DSO_EINVAL.  The paper has no counterpart. */
 dso_status dso_set_norm_check(dso_ctx* ctx, double tol);
 
-/* Set psi ([S][grid], complex128 or complex64 by the context's precision)
- * from host or device memory. */
+/* Set psi ([B][S][grid], complex128 or complex64 by the context's
+ * precision) from host or device memory.  Host data is staged on the
+ * device and checked there: a non-finite value returns DSO_ENUMERIC and
+ * leaves psi unchanged; the call returns when the host buffer may be reused.
+ * Device data is copied on the context's stream without a check. */
 dso_status dso_set_psi(dso_ctx* ctx, const void* psi, int where);
 
 /* Advance psi by time t with step dt (dt may be negative; t/dt must be a
