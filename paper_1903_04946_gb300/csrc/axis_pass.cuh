@@ -530,6 +530,25 @@ __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, 
                                               const SmemLayout lay, const PassArgs* dbg = nullptr) {
   const int tile_pts = G * L;
   const int tile_sz = G * lay.ls;
+  if (tg.stride_log2 == 0) {  // contiguous lines: the tile's phases are one block
+    const C* blk = tau + (size_t)tg.o0 * L;
+    for (int e = tid; e < tile_pts; e += nthr) {
+      const int g = e >> Plan<L>::log2L, n = e & (L - 1);
+#ifdef DSO_DEBUG_BOUNDS
+      if (dbg && !DSO_CHECK_INDEX((long long)(&blk[e] - (const C*)dbg->tau_base), dbg->tau_elems, 103, dbg->err))
+        continue;
+#endif
+      C t = __ldg(&blk[e]);
+      if (scale != (RealT<C>)1) t = cscale(t, scale);
+      const int off = g * lay.ls + lay.pos(n);
+      for (int s = 0; s < SVl; ++s) {
+        C* p = &sm[s * tile_sz + off];
+        *p = cmul(*p, t);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int e = tid; e < tile_pts; e += nthr) {
     int g, n;
     tile_elem<L>(e, tg, g, n);
@@ -577,9 +596,19 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   const int tile_sz = G * lay.ls;  // shared-memory elements per staged surface
 
   pdl_wait();  // psi is the previous pass's output
-  // load
+  // load (lines along the contiguous axis: the tile is one contiguous block)
+  const bool contig = a.stride_log2 == 0;
   for (int s = 0; s < SV; ++s) {
     const C* src = psi + (size_t)(surf0 + s) * a.P;
+    if (contig) {
+      const C* blk = src + (size_t)tg.o0 * L;
+      for (int e = tid; e < tile_pts; e += nthr) {
+        const int g = e >> Plan<L>::log2L, n = e & (L - 1);
+        if (DSO_CHECK_INDEX((long long)(surf0 + s) * a.P + tg.o0 * L + e, a.psi_elems, 100, a.err))
+          sm[s * tile_sz + g * lay.ls + lay.pos(n)] = blk[e];
+      }
+      continue;
+    }
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, tg, g, n);
@@ -621,6 +650,15 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   // store
   for (int s = 0; s < SV; ++s) {
     C* dst = psi + (size_t)(surf0 + s) * a.P;
+    if (contig) {
+      C* blk = dst + (size_t)tg.o0 * L;
+      for (int e = tid; e < tile_pts; e += nthr) {
+        const int g = e >> Plan<L>::log2L, n = e & (L - 1);
+        if (DSO_CHECK_INDEX((long long)(surf0 + s) * a.P + tg.o0 * L + e, a.psi_elems, 101, a.err))
+          blk[e] = sm[s * tile_sz + g * lay.ls + lay.pos(n)];
+      }
+      continue;
+    }
     for (int e = tid; e < tile_pts; e += nthr) {
       int g, n;
       tile_elem<L>(e, tg, g, n);
