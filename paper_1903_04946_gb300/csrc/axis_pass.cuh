@@ -596,8 +596,13 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   const int tile_sz = G * lay.ls;  // shared-memory elements per staged surface
 
   pdl_wait();  // psi is the previous pass's output
-  // load (lines along the contiguous axis: the tile is one contiguous block)
+  // load.  Two common tile shapes are addressed directly: lines along the
+  // contiguous axis (the tile is one contiguous block), and tiles of G
+  // consecutive inner positions of one outer row (G <= stride: element
+  // (n, i) sits at row + n * stride + i).
   const bool contig = a.stride_log2 == 0;
+  const bool one_row = !contig && a.G_log2 <= a.stride_log2;
+  const long long row = ((tg.o0 * L) << a.stride_log2) + tg.i0;  // first element of a one-row tile
   for (int s = 0; s < SV; ++s) {
     const C* src = psi + (size_t)(surf0 + s) * a.P;
     if (contig) {
@@ -606,6 +611,16 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
         const int g = e >> Plan<L>::log2L, n = e & (L - 1);
         if (DSO_CHECK_INDEX((long long)(surf0 + s) * a.P + tg.o0 * L + e, a.psi_elems, 100, a.err))
           sm[s * tile_sz + g * lay.ls + lay.pos(n)] = blk[e];
+      }
+      continue;
+    }
+    if (one_row) {
+      const C* blk = src + row;
+      for (int e = tid; e < tile_pts; e += nthr) {
+        const int i = e & (G - 1), n = e >> a.G_log2;
+        const long long off = ((long long)n << a.stride_log2) + i;
+        if (DSO_CHECK_INDEX((long long)(surf0 + s) * a.P + row + off, a.psi_elems, 100, a.err))
+          sm[s * tile_sz + i * lay.ls + lay.pos(n)] = blk[off];
       }
       continue;
     }
@@ -656,6 +671,16 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
         const int g = e >> Plan<L>::log2L, n = e & (L - 1);
         if (DSO_CHECK_INDEX((long long)(surf0 + s) * a.P + tg.o0 * L + e, a.psi_elems, 101, a.err))
           blk[e] = sm[s * tile_sz + g * lay.ls + lay.pos(n)];
+      }
+      continue;
+    }
+    if (one_row) {
+      C* blk = dst + row;
+      for (int e = tid; e < tile_pts; e += nthr) {
+        const int i = e & (G - 1), n = e >> a.G_log2;
+        const long long off = ((long long)n << a.stride_log2) + i;
+        if (DSO_CHECK_INDEX((long long)(surf0 + s) * a.P + row + off, a.psi_elems, 101, a.err))
+          blk[off] = sm[s * tile_sz + i * lay.ls + lay.pos(n)];
       }
       continue;
     }
