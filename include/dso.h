@@ -248,9 +248,15 @@ int64_t dso_launch_count(const dso_ctx* ctx);
  * legacy default stream) on the calling thread's current device and does
  * not synchronise.
  *
+ * psi must be 16-byte aligned and V and out 8-byte aligned (DSO_EINVAL
+ * otherwise: a misaligned element pointer would fault the kernel).
+ *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress with that device current); make that first call
- * before capturing the stream into a CUDA graph.  Every call on a device
+ * before capturing the stream into a CUDA graph.  The address is kept with
+ * the device's driver context and looked up again when that context changes
+ * (for example after cudaDeviceReset); a call that is captured into a graph
+ * keeps the address of the context it was captured in.  Every call on a device
  * shares the one array and leaves its partial sums there; each call writes
  * every slot it reads before reading it, so nothing is cleared between
  * calls.  Calls that overlap on the GPU (other streams, other host threads)

@@ -265,18 +265,43 @@ def dso_launch_count(ctx) -> int:
 def dso_position_observables_noalloc(psi, V, S, P, dV, out, stream=None):
     """Allocation-free populations and potential energy of a device psi.
     psi, V (or None) and out are CUDA tensors; out receives S + 1 doubles.
-    For callers that cannot allocate device memory; see include/dso.h."""
-    pp, wp = _ptr(psi)
-    po, wo = _ptr(out, writable=True)
-    if wp != DSO_DEVICE or wo != DSO_DEVICE:
-        raise ValueError("psi and out must be device tensors")
-    pv = None
-    if V is not None:
-        pv, wv = _ptr(V)
-        if wv != DSO_DEVICE:
-            raise ValueError("V must be a device tensor")
-    _check(load().dso_position_observables_noalloc(pp, pv, int(S), int(P), float(dV), po,
-                                                    _stream_handle(stream)), "dso_position_observables_noalloc")
+    For callers that cannot allocate device memory; see include/dso.h.
+
+    The C entry point receives no buffer sizes, so the element types and
+    counts are checked here, before anything is launched: psi complex128 with
+    at least S * P elements, V float64 with at least S(S+1)/2 * P, out float64
+    with at least S + 1, all on one GPU (the call runs with that GPU
+    current)."""
+    import torch
+    S, P = int(S), int(P)
+    if not isinstance(psi, torch.Tensor) or not isinstance(out, torch.Tensor) or \
+            (V is not None and not isinstance(V, torch.Tensor)):
+        raise TypeError("psi, V and out must be torch tensors")
+    if psi.dtype != torch.complex128:
+        raise ValueError("psi must be complex128")
+    if out.dtype != torch.float64:
+        raise ValueError("out must be float64")
+    if S >= 1 and P >= 1:
+        if psi.numel() < S * P:
+            raise ValueError(f"psi holds {psi.numel()} elements, needs S * P = {S * P}")
+        if out.numel() < S + 1:
+            raise ValueError(f"out holds {out.numel()} elements, needs S + 1 = {S + 1}")
+        if V is not None:
+            if V.dtype != torch.float64:
+                raise ValueError("V must be float64")
+            if V.numel() < S * (S + 1) // 2 * P:
+                raise ValueError(f"V holds {V.numel()} elements, needs S(S+1)/2 * P = {S * (S + 1) // 2 * P}")
+    tensors = [psi, out] + ([V] if V is not None else [])
+    if not all(t.is_cuda for t in tensors):
+        raise ValueError("psi, V and out must be device tensors")
+    if len({t.device for t in tensors}) != 1:
+        raise ValueError("psi, V and out must be on one device")
+    pp, _ = _ptr(psi)
+    po, _ = _ptr(out, writable=True)
+    pv = _ptr(V)[0] if V is not None else None
+    with torch.cuda.device(psi.device):
+        _check(load().dso_position_observables_noalloc(pp, pv, S, P, float(dV), po, _stream_handle(stream)),
+               "dso_position_observables_noalloc")
     return out
 
 

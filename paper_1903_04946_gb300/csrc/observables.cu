@@ -9,7 +9,11 @@
 // Two launches: per-block partial sums (each block walks a fixed strided set
 // of grid points), then one block adds the partials in block order, so the
 // result does not depend on scheduling.  The caller applies dV.
+#include <stdint.h>
+
 #include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "../../include/dso.h"
 #include "dso_internal.h"
@@ -127,8 +131,29 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocBlocks * kNoA
 // Host-side device addresses of g_noalloc_partials, one per device.  The
 // array's name in host code is only a host stand-in for the symbol, so the
 // address must come from cudaGetSymbolAddress with that device current.
+// The driver context the address belongs to is kept beside it: after a
+// device reset the module is loaded again in a new context and the array may
+// sit elsewhere, so a changed context means looking the address up again.
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[64] = {};
+CUcontext g_noalloc_ctx[64] = {};
+
+// The calling thread's current driver context (cuCtxGetCurrent, looked up
+// once through the runtime so the library needs no -lcuda), or null.
+CUcontext current_driver_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuCtxGetCurrent_v4000)f;
+  });
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 __global__ void obs_position_partial_kernel(const double2* __restrict__ psi, const double* __restrict__ V, int S,
                                             long long P, double* __restrict__ partials) {
@@ -186,16 +211,22 @@ extern "C" dso_status dso_position_observables_noalloc(const void* psi, const do
   if (!psi || !out) return DSO_EINVAL;
   if (S < 1 || S + 1 > kNoAllocCols || S > DSO_MAX_SURFACES) return DSO_EINVAL;  // scratch holds S <= 4
   if (P < 1) return DSO_EINVAL;
+  // misaligned element pointers would fault the kernels (a sticky error that
+  // ends the caller's CUDA context): reject them here
+  if ((uintptr_t)psi % 16 != 0 || (uintptr_t)out % 8 != 0 || (V && (uintptr_t)V % 8 != 0)) return DSO_EINVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DSO_ECUDA;
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      // first call on this device: look up the array's device address
+    const CUcontext cur = current_driver_context();
+    if (!g_noalloc_ptr[dev] || cur != g_noalloc_ctx[dev]) {
+      // first call on this device (or in a new context of it): look up the
+      // array's device address with the device current
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_partials) != cudaSuccess || !ptr) return DSO_ECUDA;
       g_noalloc_ptr[dev] = (double*)ptr;
+      g_noalloc_ctx[dev] = current_driver_context();
     }
     scratch = g_noalloc_ptr[dev];
   }

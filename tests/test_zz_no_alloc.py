@@ -35,6 +35,23 @@ def test_noalloc_populations_match_context_observables():
         assert res[:pr.S] == pytest.approx(pops, rel=1e-12, abs=1e-15), call
         assert np.sqrt(res[:pr.S].sum()) == pytest.approx(norm, rel=1e-13), call
         assert res[pr.S] == pytest.approx(vref, rel=1e-12), call
+    # without a potential the last slot is exactly zero
+    out = torch.full((pr.S + 1,), float("nan"), dtype=torch.float64, device="cuda")
+    dso.dso_position_observables_noalloc(psi, None, pr.S, pr.points, dV, out, stream)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy()
+    assert res[pr.S] == 0.0
+    assert res[:pr.S] == pytest.approx(pops, rel=1e-12, abs=1e-15)
+    # the calls allocate nothing: free device memory does not move over
+    # repeated calls once the first call has run
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        dso.dso_position_observables_noalloc(psi, V, pr.S, pr.points, dV, out, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     # a surface count beyond the scratch array is rejected
+    big = torch.zeros(6, dtype=torch.float64, device="cuda")
     with pytest.raises(dso.DSOError):
-        dso.dso_position_observables_noalloc(psi, None, 5, pr.points, dV, out, stream)
+        dso.dso_position_observables_noalloc(psi.reshape(-1)[: 5 * (pr.points // 5) * 1], None, 5,
+                                             pr.points // 5, dV, big, stream)
