@@ -239,10 +239,11 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch (read + write) of `kernel` from the committed ncu
-    summaries, or None when no summary covers it or the kernel sources have
-    changed since the counters were taken."""
+def profiled_value(kernel: str, key: str):
+    """A per-launch figure of `kernel` recorded in the committed ncu summaries
+    as a line "<key>: `<kernel>` = <integer>", with the summary it came from,
+    or None when no summary covers it or the kernel sources have changed since
+    the counters were taken."""
     import glob
     import re
     want = kernel_sources_hash()
@@ -252,10 +253,16 @@ def profiled_traffic(kernel: str):
         m = re.search(r"kernel_sources_sha256_16 = ([0-9a-f]{16})", text)
         if not m or m.group(1) != want:
             continue
-        for k, v in re.findall(r"traffic_bytes_per_launch: `(.+?)` = (\d+)", text):
+        for k, v in re.findall(re.escape(key) + r": `(.+?)` = (\d+)", text):
             if k == kernel:
                 return int(v), os.path.relpath(path, ROOT)
     return None
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch (read + write) of `kernel` from the committed ncu
+    summaries (see profiled_value)."""
+    return profiled_value(kernel, "traffic_bytes_per_launch")
 
 
 def run_gpu(args):
@@ -351,6 +358,38 @@ def run_gpu(args):
     e2e = {"value": job_throughput(world, pts, nsub, e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": bytes_psi, "d2h_bytes_per_step": bytes_psi}
 
+    # the product's replay path: one dso_propagate call of K steps (the first
+    # step's passes, K - 1 replays of the captured CUDA graph, the final
+    # pass).  Timed once on the device (CUDA events on the context's stream)
+    # and once end to end through the public API with psi copied in from and
+    # out to pinned host memory around the call.  No L2 flush inside the call:
+    # the 64^3 x 3 FP64 state (12.6 MB) stays in the 129 MB L2 between steps.
+    kg = args.steps
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    with torch.cuda.stream(stream):
+        flush.fill_(-1.0)
+        g0.record(stream)
+        ctx.propagate(kg * DT, DT)
+        g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = max_over_ranks(g0.elapsed_time(g1), world, f"cuda:{device}")
+    barrier()
+    t0 = time.perf_counter()
+    dso.dso_set_psi(ctx.ctx, host_in)
+    ctx.propagate(kg * DT, DT)
+    dso.dso_get_psi(ctx.ctx, host_out)
+    torch.cuda.synchronize()
+    graph_e2e_s = max_over_ranks(time.perf_counter() - t0, world, f"cuda:{device}")
+    barrier()
+    graph = {"value": job_throughput(world, pts, nsub, kg, graph_ms * 1e-3), "unit": UNIT, "steps": kg,
+             "ms_per_step": graph_ms / kg,
+             "e2e": {"value": job_throughput(world, pts, nsub, kg, graph_e2e_s), "unit": UNIT,
+                     "h2d_bytes_per_call": bytes_psi, "d2h_bytes_per_call": bytes_psi},
+             "note": "one propagate(K*dt, dt) call: first step, K-1 CUDA-graph replays, final pass; "
+                     "no L2 flush inside the call"}
+
     # per-kernel durations with CUDA events around every launch (same sizes,
     # same pass list as the timed steps)
     kinds = dso.dso_profile_steps(ctx.ctx, DT, max(2, min(args.steps, 10)))
@@ -376,7 +415,9 @@ def run_gpu(args):
                     "peak_source": "FP64 unit count x max SM clock (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
     roofline.update({
                 "kernel": kind_name(dom), "kernel_avg_us": round(dom["avg_ms"] * 1e3, 2),
-                "kernel_share_of_step": round(dom["ms_per_step"] / prof_step_ms, 4),
+                "kernel_share_of_step": round(dom["ms_per_step"] / (ms / args.steps), 4),
+                "kernel_share_of_profiled_step": round(dom["ms_per_step"] / prof_step_ms, 4),
+                "profiled_step_ms": round(prof_step_ms, 4),
                 "hbm_gbs_achieved": round(dom["bytes"] / (dom["avg_ms"] * 1e-3) / 1e9, 1),
                 "kinds": [{"kernel": kind_name(k), "avg_us": round(k["avg_ms"] * 1e3, 2),
                            "launches_per_step": k["launches_per_step"], "tile_lines": k["tile_lines"],
@@ -388,6 +429,23 @@ def run_gpu(args):
     if tr is not None:
         roofline["traffic"] = tr[0]
         roofline["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, {tr[1]}"
+    if not fp32:
+        # instruction-rate roofline of the same kernel: FP64 instructions per
+        # launch (ncu count from the committed summary of these kernel
+        # sources) over its event-timed duration, against the FP64 FMA rate
+        # this GPU sustains, measured now by a microbenchmark
+        try:
+            rate = dso.dso_fp64_issue_rate(device)
+        except Exception:  # noqa: BLE001 (diagnostic only)
+            rate = None
+        dp = profiled_value(roofline["kernel"], "dp_inst_per_launch")
+        fp = {"measured_peak_inst_per_s": rate,
+              "peak_source": "dso_fp64_issue_rate: DFMA chains with register operands, measured in this run"}
+        if dp is not None and rate:
+            achieved_i = dp[0] / (dom["avg_ms"] * 1e-3)
+            fp.update(inst_per_launch=dp[0], achieved_inst_per_s=achieved_i, frac=round(achieved_i / rate, 4),
+                      inst_source=f"ncu smsp__sass_thread_inst_executed_op_d{{add,fma,mul}}_pred_on, {dp[1]}")
+        roofline["fp64_inst"] = fp
     # the autotuned kernel configuration; DSO_PLAN=<this> reproduces it (profiling)
     roofline["plan"] = dso.dso_tuned_plan(ctx.ctx)
 
@@ -410,10 +468,20 @@ def run_gpu(args):
                                                                        np.sum(np.abs(a64) ** 2))),
                      "norm_drift": float(abs(n32 - 1.0)), "reference": "FP64 GPU path, same input and steps"}
 
+    ctx.close()
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras and W.get("name", "pyrazine64") == "pyrazine64":
+        for key, fn in (("precision", sub_precision), ("time_to_target", sub_time_to_target),
+                        ("serving", sub_serving)):
+            t_sub = time.perf_counter()
+            try:
+                extras[key] = fn(device)
+            except Exception as ex:  # noqa: BLE001 (a failed sub-record must not hide the main line)
+                extras[key] = {"error": f"{type(ex).__name__}: {ex}"}
+            extras[key]["bench_seconds"] = round(time.perf_counter() - t_sub, 2)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sample_substeps=args.cpu_substeps)
-    ctx.close()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,11 +491,13 @@ def run_gpu(args):
                 "config": config_dict({"l2": "flushed before every timed step (256 MiB write outside the "
                                              "per-step CUDA events)",
                                        "substeps_per_step": nsub, "grid_points": pts}),
-                "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk}
+                "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
+                "graph_replay": graph}
         if cpu is not None:
             line["cpu_baseline"] = cpu
         if precision is not None:
             line["precision"] = precision
+        line.update(extras)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -435,13 +505,171 @@ def run_gpu(args):
 
 
 # --------------------------------------------------------------------------
+# Sub-records: the other two parts of the metric and the FP32 mode, each
+# bounded to a few tens of seconds (rank 0, N = 1 only)
+# --------------------------------------------------------------------------
+
+def _hbm_peak():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def sub_precision(device, steps=10, warmup=3, check_steps=4):
+    """FP32 storage-and-FFT mode on the 128^3 three-surface model, triple
+    jump order 4: device-timed steps (L2 flushed before each), the step's
+    roofline counted with algorithmic bytes -- psi read and written once per
+    fused pass pair (32 B per amplitude-substep in FP32) plus the operator
+    tables read (the loaded potential entries and the kinetic phase, 8 B
+    each per grid point) -- and the error against the FP64 path."""
+    import numpy as np
+    import torch
+
+    import paper_1903_04946_gb300 as dso
+    import synth
+    n, S_, order, dt = (128, 128, 128), 3, 4, T_FINAL / 128
+    pr = synth.pyrazine_like(seed=SEED, n=n, S=S_)
+    pts = int(np.prod(n))
+    a, b, *_ = dso.dso_scheme_coefficients(order, dso.DSO_TRIPLE_JUMP)
+    nsub = len(b)
+    stream = torch.cuda.Stream(device=device)
+    ctx = dso.Context(device=device, stream=stream, precision=dso.DSO_FP32)
+    ctx.load_problem(pr)
+    dso.dso_set_scheme(ctx.ctx, order, dso.DSO_TRIPLE_JUMP)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
+    for _ in range(warmup):
+        ctx.propagate(dt, dt)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            ctx.propagate(dt, dt)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+    ctx.close()
+    # surface 0 is uncoupled in this model: the potential step reads 4 of the
+    # 6 packed entries (S(S+1)/2 - (S-1)); plus one kinetic phase per point
+    tab_entries = S_ * (S_ + 1) // 2 - (S_ - 1) + 1
+    bytes_step = nsub * (32 * S_ * pts + 8 * tab_entries * pts)
+    peak, src = _hbm_peak()
+    gbs = bytes_step / (ms * 1e-3) / 1e9
+    c32 = dso.Context(pr, device=device, order=order, scheme=dso.DSO_TRIPLE_JUMP, precision=dso.DSO_FP32)
+    c64 = dso.Context(pr, device=device, order=order, scheme=dso.DSO_TRIPLE_JUMP, precision=dso.DSO_FP64)
+    c32.propagate(check_steps * dt, dt)
+    c64.propagate(check_steps * dt, dt)
+    a32, a64 = c32.psi().astype(np.complex128), c64.psi()
+    n32, _, _ = c32.observables()
+    c32.close()
+    c64.close()
+    err = float(np.sqrt(np.sum(np.abs(a32 - a64) ** 2) / np.sum(np.abs(a64) ** 2)))
+    return {"workload": "pyrazine-like 3-D, 3 surfaces, 128^3 grid per surface, complex64 storage and FFT "
+                        "(FP64 angles, coefficients and reductions), triple jump order 4, dt = 2000/128 a.u.",
+            "value": pts * nsub / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "substeps_per_step": nsub, "l2": "flushed before every timed step",
+            "roofline": {"bound": "hbm", "bytes_per_step": bytes_step, "achieved": round(gbs, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
+                         "bytes": "algorithmic: 32 B per amplitude-substep (psi read + written by two fused "
+                                  "passes) + 8 B per grid point per table entry read (4 potential entries, "
+                                  "1 kinetic phase)"},
+            "error_vs_fp64": {"steps": check_steps, "rel_l2": err, "norm_drift": float(abs(n32 - 1.0)),
+                              "reference": "FP64 GPU path, same input and steps"}}
+
+
+def sub_time_to_target(device, grid=32, batch=4, tf=2000.0, target=1e-10, ref_k=8, order=6):
+    """Time to a wavefunction error of 1e-10 (Sec. III efficiency study) for
+    Suzuki order 6 on pyrazine-like three-surface models on a grid^3 grid,
+    t = tf: the single path (job 0 alone, dt = tf/2^k halved until its error
+    against the reference is <= target) and the batched path (all `batch`
+    jobs of the same shape in one context, each job's error checked), with
+    the reference Suzuki 10 at dt = tf/2^ref_k (checked against its own run
+    at 2 dt).  The CPU oracle's time for the single path's propagation is
+    extrapolated from its measured time per substep (marked as such)."""
+    import numpy as np
+
+    from paper_1903_04946_gb300 import efficiency as E
+    import synth
+    n = (grid, grid, grid)
+    base = synth.pyrazine_like(seed=SEED, n=n)
+    jobs = [base]
+    for b in range(1, batch):
+        pr = synth.pyrazine_like(seed=SEED + 1000 + b, n=n)
+        pr.mass = base.mass
+        jobs.append(pr)
+    t0 = time.perf_counter()
+    ref, ref_secs = E._propagate(jobs, "suzuki", 10, tf, ref_k, True)
+    ref_c, _ = E._propagate(jobs, "suzuki", 10, tf, ref_k - 1, True)
+    ref_err = max(E._err(jobs[j], ref_c[j], ref[j]) for j in range(batch))
+    single = None
+    for k in range(8, 13):
+        psi, secs = E._propagate(jobs[:1], "suzuki", order, tf, k, False)
+        e = E._err(jobs[0], psi, ref[0])
+        if e <= target:
+            single = {"k": k, "dt": tf / 2 ** k, "error": e, "seconds": secs}
+            break
+    batched = None
+    for k in range(8, 13):
+        psi, secs = E._propagate(jobs, "suzuki", order, tf, k, True)
+        errs = [E._err(jobs[j], psi[j], ref[j]) for j in range(batch)]
+        if max(errs) <= target:
+            batched = {"k": k, "dt": tf / 2 ** k, "max_error": max(errs), "seconds": secs,
+                       "per_wavepacket_seconds": secs / batch}
+            break
+    out = {"workload": f"pyrazine-like 3-D, 3 surfaces, {grid}^3 grid per surface, complex128, t = {tf} a.u., "
+                       f"Suzuki order {order}; {batch} jobs with their own couplings and packets",
+           "target": target, "reference": {"scheme": "suzuki", "order": 10, "dt": tf / 2 ** ref_k,
+                                           "error_of_run_at_2dt": ref_err},
+           "single": single, "batched": batched}
+    if single and batched:
+        out["batched_vs_single_per_wavepacket"] = single["seconds"] / batched["per_wavepacket_seconds"]
+    if single:
+        # the oracle's time per substep on this shape, times the substeps the
+        # single path needed: an extrapolation, not a run to the target
+        from oracle import propagate as P
+        prop = P.Propagator(jobs[0])
+        seq = P.action_sequence(P.VTV, order, "suzuki")
+        pairs = [(seq[i], seq[i + 1]) for i in range(0, len(seq) - 1, 2)]
+        dt = single["dt"]
+        for (_, a), (_, b) in pairs:
+            prop.potential_unitary(a * dt)
+            prop.kinetic_unitary(b * dt)
+        psi = jobs[0].psi0.copy()
+        c0 = time.perf_counter()
+        for (_, a), (_, b) in pairs[:5]:
+            psi = prop.apply_T(prop.apply_V(psi, a * dt), b * dt)
+        per_sub = (time.perf_counter() - c0) / 5
+        substeps = 2 ** single["k"] * len(pairs)
+        out["cpu_oracle"] = {"seconds_extrapolated": per_sub * substeps, "seconds_per_substep": per_sub,
+                             "substeps": substeps, "cores": 1,
+                             "note": "extrapolated: measured time of 5 substeps x substeps of the single path"}
+    out["wall_seconds"] = time.perf_counter() - t0
+    return out
+
+
+def sub_serving(device, n_jobs=20, load=0.8, max_points=1 << 19, seed=1907):
+    """A short seeded Poisson stream of mixed propagation jobs through the
+    continuous-batching serving loop: p50/p99 latency and throughput."""
+    from paper_1903_04946_gb300 import serving
+    jobs = serving.make_jobs(n_jobs, seed, load, max_points)
+    srv = serving.Server(device=device)
+    stats = srv.run(jobs)
+    stats.update(workload=f"seeded Poisson stream of {n_jobs} jobs: D in {{1,2,3}}, 2^8..{max_points} points per "
+                          "surface, S in {2,3,4}, triple-jump orders 2-8, t in [500, 5000] a.u., complex128",
+                 load=load, seed=seed)
+    return stats
+
+
+# --------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
 
-def _oracle_substep_runner():
+def _oracle_substep_runner(seed=SEED):
     import numpy as np
     from oracle import propagate as P
-    pr = workload(SEED)
+    pr = workload(seed)
     prop = P.Propagator(pr)
     seq = P.action_sequence(P.VTV, ORDER, SCHEME_NAME)
     # one substep = the potential action before a kinetic action plus that
@@ -455,41 +683,105 @@ def _oracle_substep_runner():
         psi = prop.apply_V(state["psi"], a * DT)
         state["psi"] = prop.apply_T(psi, b * DT)
         state["i"] += 1
+
+    # the operators of every coefficient (the oracle caches one per value),
+    # built before any timing as the GPU path builds its tables
+    for (_, a), (_, b) in pairs:
+        prop.potential_unitary(a * DT)
+        prop.kinetic_unitary(b * DT)
     return one, int(np.prod(N_GRID))
 
 
-def cpu_baseline(sample_substeps=20):
+_SINGLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def _oracle_worker_init(barrier, workload_name, order):
+    global _BARRIER
+    _BARRIER = barrier
+    select_workload(workload_name, order)
+
+
+def _oracle_worker(job):
+    """Runs in a spawned process: the oracle, single-threaded, on its own
+    seeded wavepacket; times `nsub` substeps after a common barrier."""
+    seed, nsub = job
+    one, pts = _oracle_substep_runner(seed)
+    one()
+    _BARRIER.wait()
+    t0 = time.time()
+    for _ in range(nsub):
+        one()
+    return t0, time.time(), pts * nsub
+
+
+def oracle_throughput(substeps, cores=None):
+    """The FP64 oracle as it stands, timed on `cores` host cores at once (all
+    of them by default): one spawned single-threaded process per core, each
+    propagating its own seeded wavepacket of the workload for `substeps`
+    substeps after a common barrier (independent problems, like the GPU's
+    replicas).  Returns (grid-pts x substeps per second over all processes,
+    cores, wall seconds of the timed region)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in _SINGLE_THREAD_ENV}
+    for k in _SINGLE_THREAD_ENV:
+        os.environ[k] = "1"  # inherited by the spawned processes
+    try:
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(cores)
+        with ctx.Pool(cores, initializer=_oracle_worker_init,
+                      initargs=(barrier, W.get("name", "pyrazine64"), W["order"])) as pool:
+            res = pool.map(_oracle_worker, [(SEED + 100 + i, substeps) for i in range(cores)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    return sum(r[2] for r in res) / (t1 - t0), cores, t1 - t0
+
+
+def cpu_baseline(sample_substeps=20, all_core_substeps=8):
+    """The oracle on one host core (this process, numpy single-threaded on
+    the workload) and on all host cores (one spawned process per core)."""
     one, pts = _oracle_substep_runner()
-    one()  # builds the cached operators
+    one()
     t0 = time.perf_counter()
     for _ in range(sample_substeps):
         one()
     dt = time.perf_counter() - t0
-    return {"value": pts * sample_substeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample_substeps} substeps (potential action + FFT/phase/inverse FFT) of the same "
-                      f"{'x'.join(map(str, N_GRID))} x {S} workload, numpy FP64 oracle, single thread"}
+    shape = f"{'x'.join(map(str, N_GRID))} x {S}"
+    out = {"value": pts * sample_substeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{sample_substeps} substeps (potential action + FFT/phase/inverse FFT) of the same "
+                     f"{shape} workload, numpy FP64 oracle, one process"}
+    if all_core_substeps > 0:
+        rate, cores, wall = oracle_throughput(all_core_substeps)
+        out["all_cores"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{cores} single-threaded processes at once, each {all_core_substeps} "
+                                      f"substeps of its own seeded {shape} wavepacket ({wall:.1f} s timed)"}
+    return out
 
 
 def run_reference(args):
+    """The oracle as the reference arm: every host core runs one
+    single-threaded oracle process on its own seeded wavepacket of the
+    workload; a step is one substep in every process (bounded sample)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    one, pts = _oracle_substep_runner()
-    for _ in range(args.warmup):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        one()
-    dt = time.perf_counter() - t0
-    value = pts * args.steps / dt
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+    rate, cores, wall = oracle_throughput(args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": config_dict({"reference_step": "one substep of the composed sequence (bounded sample)"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} substeps of the 64^3 x 3 workload"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": config_dict({"reference_step": f"one substep of the composed sequence in each of {cores} "
+                                                     "oracle processes (bounded sample)"}),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} substeps in each of {cores} single-threaded processes, "
+                                       f"each on its own seeded {'x'.join(map(str, N_GRID))} x {S} wavepacket"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -501,6 +793,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-substeps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sub-records (FP32 precision mode, time to 1e-10, serving)")
     ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
     ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
     ap.add_argument("--profile-steps", type=int, default=0,

@@ -266,6 +266,16 @@ int64_t dso_launch_count(const dso_ctx* ctx);
 dso_status dso_position_observables_noalloc(const void* psi, const double* V, int S, int64_t P, double dV,
                                             double* out, void* cuda_stream);
 
+/* Diagnostics: the rate (instructions per second, written to *inst_per_s)
+ * at which CUDA device `device` retires FP64 fused multiply-adds with all
+ * three operands in per-thread registers -- the operand pattern of the FFT
+ * butterflies, potential matvecs and kinetic phases of the FP64 path, which
+ * is bound by the FP64 pipe.  Runs a short microbenchmark (a few
+ * tens of milliseconds) on a stream of its own and synchronises it; the best of three
+ * timed launches is reported.  The paper has no counterpart: this is the
+ * denominator of the instruction-rate roofline of the FP64 kernels. */
+dso_status dso_fp64_issue_rate(int device, double* inst_per_s);
+
 /* Message for the last failed call on this thread (never NULL; valid until
  * the next call on this thread). */
 const char* dso_last_error(void);

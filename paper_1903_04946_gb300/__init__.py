@@ -27,7 +27,7 @@ EXPORTS = (
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
     "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan", "dso_set_composition",
-    "dso_composition_coefficients", "dso_set_norm_check",
+    "dso_composition_coefficients", "dso_set_norm_check", "dso_fp64_issue_rate",
 )
 
 _lib = None
@@ -72,6 +72,7 @@ def load(path: str = LIB):
         "dso_composition_coefficients": (i32, [i32, pd, pi, pi, pd, pd, pi, pi, pi, pi]),
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
+        "dso_fp64_issue_rate": (i32, [i32, pd]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -303,6 +304,13 @@ def dso_position_observables_noalloc(psi, V, S, P, dV, out, stream=None):
         _check(load().dso_position_observables_noalloc(pp, pv, S, P, float(dV), po, _stream_handle(stream)),
                "dso_position_observables_noalloc")
     return out
+
+
+def dso_fp64_issue_rate(device: int = 0) -> float:
+    """FP64 FMA instructions per second the device retires (microbenchmark)."""
+    r = ctypes.c_double()
+    _check(load().dso_fp64_issue_rate(int(device), ctypes.byref(r)), "dso_fp64_issue_rate")
+    return r.value
 
 
 def dso_last_error() -> str:
