@@ -68,8 +68,9 @@ enum { DSO_VTV = 0, DSO_TVT = 1, DSO_VT = 2, DSO_TV = 3 };
 #define DSO_MAX_DIM 3
 #define DSO_MAX_SURFACES 4
 #define DSO_MIN_AXIS 8
-#define DSO_MAX_AXIS 4096
-#define DSO_MAX_AXIS_1D 8192  /* a 1-D grid may be this long */
+#define DSO_MAX_AXIS (1 << 22)      /* points on one axis, any D */
+#define DSO_MAX_AXIS_1D DSO_MAX_AXIS
+#define DSO_MAX_POINTS (1LL << 30)  /* grid points per surface */
 
 /* Create a context on CUDA device `device`.  precision DSO_FP64 keeps psi,
  * the operator tables and the FFTs in FP64; DSO_FP32 stores psi and the
@@ -85,12 +86,13 @@ dso_status dso_create(dso_ctx** out, int device, int precision, void* cuda_strea
 void dso_destroy(dso_ctx* ctx);
 
 /* Grid of Sec. II G / App. B: D in 1..DSO_MAX_DIM axes, n[d] a power of two
- * in [DSO_MIN_AXIS, DSO_MAX_AXIS] (a 1-D grid up to DSO_MAX_AXIS_1D),
+ * in [DSO_MIN_AXIS, DSO_MAX_AXIS], at most DSO_MAX_POINTS points in all,
  * qmax[d] > qmin[d] (host arrays of length D).  Resets any loaded potential,
- * masses, state and tables.  With S surfaces, a grid of D >= 2 needs
- * S * n[0] <= 8192 (the potential pass holds all surfaces of an axis-0
- * line); a 1-D grid longer than that runs its potential and kinetic steps
- * as separate passes. */
+ * masses, state and tables.  An axis longer than 4096 points (or an axis 0
+ * whose S surfaces exceed 8192 points in all) is transformed as two axes of
+ * n1 x n2 points with twiddles between them (a four-step FFT), which the
+ * library arranges by itself; the kernel passes then run over these
+ * "virtual" axes (dso_profile_steps and dso_tuned_plan number them). */
 dso_status dso_set_grid(dso_ctx* ctx, int D, const int64_t* n, const double* qmin,
                         const double* qmax);
 
@@ -193,7 +195,7 @@ dso_status dso_scheme_coefficients(int order, int scheme, int* n_a, int* n_b, do
 /* Diagnostics: advance psi by `nsteps` time steps of the current scheme
  * (the pass list of the steps after the first) with plain launches and a
  * CUDA event pair around every kernel on the context's stream, then report
- * per kind of pass: axis, flags (bit 0 inverse FFT first, bit 1 forward FFT,
+ * per kind of pass: (virtual) axis, flags (bit 0 inverse FFT first, bit 1 forward FFT,
  * bit 2 kinetic phase + inverse FFT, bit 8 one potential unitary, bit 9 a
  * second one, bit 10 a second kinetic phase), surfaces staged per tile, launches per time step and the
  * average duration of one launch in milliseconds, and the tile line count
@@ -213,7 +215,8 @@ int dso_busy(const dso_ctx* ctx);
 
 /* The kernel configuration the autotuner chose for this context, written to
  * `out` (capacity `cap` bytes, NUL-terminated) as entries
- * "axis,staged,variant,tile_lines,ctas_per_sm;" where staged is 0 for passes
+ * "axis,staged,variant,tile_lines,ctas_per_sm;" (axis: the virtual axis of
+ * the passes, see dso_set_grid) where staged is 0 for passes
  * staging one surface and 1 for passes staging all S, and variant is 0 (one
  * CTA per tile), 1 (persistent, cp.async), 2 (TMA) or 3 (persistent, TMA).
  * Setting the environment variable DSO_PLAN to such a string before the

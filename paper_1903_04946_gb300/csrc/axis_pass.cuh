@@ -569,6 +569,33 @@ __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, 
   __syncthreads();
 }
 
+// Four-step twiddles of a split axis (see VLayout): the element at position
+// k1 of a line along the first factor, whose line sits at index i2 of the
+// second factor, is multiplied by w_n^(k1 i2) after the forward FFT along the
+// line, or by its conjugate before the inverse FFT.  The table is laid out
+// [n1][n2], so the factor of (k1, i2) is xtw[k1 n2 + i2].
+template <int L, bool CONJ, typename C>
+__device__ __forceinline__ void apply_split_twiddles(C* sm, const C* __restrict__ xtw, const TileGeom& tg, int G,
+                                                     int SVl, int n2_log2, int s2_log2, int tid, int nthr,
+                                                     const SmemLayout lay) {
+  const int tile_pts = G * L;
+  const int tile_sz = G * lay.ls;
+  const long long n2_mask = (1LL << n2_log2) - 1;
+  for (int e = tid; e < tile_pts; e += nthr) {
+    int g, n;
+    tile_elem<L>(e, tg, g, n);
+    const long long i = tg.i0 + (g & (tg.Wi - 1));  // inner index of the line
+    const long long i2 = (i >> s2_log2) & n2_mask;
+    const C w = __ldg(&xtw[((long long)n << n2_log2) + i2]);
+    const int off = g * lay.ls + lay.pos(n);
+    for (int s = 0; s < SVl; ++s) {
+      C* p = &sm[(size_t)s * tile_sz + off];
+      *p = CONJ ? cmulc(*p, w) : cmul(*p, w);
+    }
+  }
+  __syncthreads();
+}
+
 // SV: surfaces staged together (S for passes with a potential step, 1 else).
 // Each thread owns one 8-element work slot per FFT stage, so a CTA has
 // SV * G * L / 8 threads; MaxThreads<L, SV> bounds it.
@@ -640,6 +667,9 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   // in address order and end with a block barrier; the FFT stages in between
   // only synchronise the threads of each line.
   if (a.flags & PASS_INV_FIRST) {
+    if (a.flags & PASS_XTW)
+      apply_split_twiddles<L, true>(sm, reinterpret_cast<const C*>(a.xtw), tg, G, SV, a.xtw_n2_log2,
+                                    a.xtw_s2_log2, tid, nthr, lay);
     fft_lines<L, true, K>(sm, tw, nslots, tid, nthr, lay);
     __syncthreads();
   }
@@ -651,7 +681,14 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
       apply_potential<L, SV>(sm, reinterpret_cast<const C*>(a.U2) + uoff, tg, G, a.stride, a.P, tid, nthr, lay,
                              &a);
   }
-  if (a.flags & PASS_FWD) fft_lines<L, false, K>(sm, tw, nslots, tid, nthr, lay);
+  if (a.flags & PASS_FWD) {
+    fft_lines<L, false, K>(sm, tw, nslots, tid, nthr, lay);
+    if (a.flags & PASS_XTW) {
+      __syncthreads();
+      apply_split_twiddles<L, false>(sm, reinterpret_cast<const C*>(a.xtw), tg, G, SV, a.xtw_n2_log2,
+                                     a.xtw_s2_log2, tid, nthr, lay);
+    }
+  }
   if (a.flags & PASS_T) {
     __syncthreads();
     apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr, (RealT<C>)1, lay, &a);

@@ -6,13 +6,16 @@
 // acting right to left in the paper's product, i.e. V(a~_1) first.  Each
 // kinetic action needs the momentum representation (Sec. II G): a forward
 // FFT over every axis, the phase, an inverse FFT over every axis.  The passes
-// (kernels over whole lines of one axis, see axis_pass.cuh) are ordered so
-// that FFTs along axis 0 are fused with the potential step and FFTs along the
-// last axis with the kinetic step:
-//   D = 1:  [V(a~_j) F0 T(b~_j) I0] per substep, final [V(a~_{NB+1})];
-//   D >= 2: [I0 V(a~_j) F0] [F1] .. [F_{D-1} T(b~_j) I_{D-1}] .. [I1] per
-//           substep; the last potential action of a step and the first of the
-//           next run in the same pass; final [I0 V(a~_{NB+1})].
+// (kernels over whole lines of one axis, see axis_pass.cuh) run over the
+// virtual axes of the grid (a grid axis longer than a pass line is two
+// virtual axes, see VLayout) and are ordered so that FFTs along virtual axis
+// 0 are fused with the potential step and FFTs along the last virtual axis
+// with the kinetic step (Dv virtual axes):
+//   Dv = 1:  [V(a~_j) F0 T(b~_j) I0] per substep, final [V(a~_{NB+1})];
+//   Dv >= 2: [I0 V(a~_j) F0] [F1] .. [F_{Dv-1} T(b~_j) I_{Dv-1}] .. [I1] per
+//            substep; the last potential action of a step and the first of
+//            the next run in the same pass; final [I0 V(a~_{NB+1})].
+// FFTs along the first factor of a split axis carry its twiddles.
 // All steps after the first have the same pass list, which is captured once
 // into a CUDA graph and replayed.
 #include <algorithm>
@@ -58,20 +61,12 @@ dso_status fail(dso_status s, const std::string& msg) {
 
 
 struct Pass {
-  int axis;
+  int axis;               // virtual axis
   int SV;
   int flags;
   int u1 = -1, u2 = -1;  // potential table indices (first, second) or -1
   int tb = -1, tb2 = -1;  // kinetic table indices (first, second) or -1
-  int L = 0;              // line length of the pass's view of the grid (0: the axis length)
 };
-
-// Long 1-D grids (S * n > 8192): the potential step cannot hold all S
-// surfaces of the one line in shared memory, so it runs as its own pointwise
-// pass over the grid viewed as lines of kVLine points (any tiling of a
-// pointwise step is exact), and the FFTs and kinetic step as a pass with one
-// surface per line.
-constexpr int kVLine = 64;
 
 Pass mkpass(int axis, int SV, int flags, int u1 = -1, int u2 = -1, int tb = -1, int tb2 = -1) {
   Pass p;
@@ -112,6 +107,11 @@ struct dso_ctx {
   // grid
   int D = 0;
   int64_t n[DSO_MAX_DIM] = {1, 1, 1};
+  // virtual axes of the passes (VLayout), fixed when S is known
+  int Dv = 0;
+  int64_t nv[DSO_MAX_VAXES] = {};
+  int vpart[DSO_MAX_VAXES] = {};     // 0 whole axis, 1 / 2 first / second factor of a split axis
+  void* xtw[DSO_MAX_VAXES] = {};     // split twiddles [n1][n2] at the first factor's index, context precision
   double qmin[DSO_MAX_DIM] = {0, 0, 0}, qmax[DSO_MAX_DIM] = {0, 0, 0};
   double mass[DSO_MAX_DIM] = {0, 0, 0};
   bool have_grid = false, have_mass = false;
@@ -150,9 +150,9 @@ struct dso_ctx {
   cudaGraphExec_t step_exec = nullptr;
   int step_exec_passes = 0;
   // tile lines and kernel variant per (axis, surfaces staged: 1 or S)
-  int G[DSO_MAX_DIM][2] = {};
-  int variant[DSO_MAX_DIM][2] = {};
-  int cps[DSO_MAX_DIM][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
+  int G[DSO_MAX_VAXES][2] = {};
+  int variant[DSO_MAX_VAXES][2] = {};
+  int cps[DSO_MAX_VAXES][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
   int pdl = 0;               // programmatic dependent launch between passes (DSO_PDL=1: on)
   unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
   int* err = nullptr;         // set by kernels whose bounded waits gave up
@@ -195,17 +195,47 @@ void drop_model(dso_ctx* c) {
   dfree(c->partials);
   dfree(c->obs_out);
   dfree(c->norm_part);
+  for (auto& x : c->xtw) dfree(x);
   c->norm_ref.clear();
   c->have_V = c->have_psi = false;
 }
 
-// A 1-D grid whose S surfaces do not fit one line tile (see kVLine).
-bool split_1d(const dso_ctx* c) { return c->D == 1 && (long long)c->S * c->n[0] > 8192; }
-
-// Line length of the passes of kind (axis d, staged surfaces 1 or S).
-int kind_L(const dso_ctx* c, int d, int which) {
-  return (d == 0 && which == 1 && split_1d(c)) ? kVLine : (int)c->n[d];
+// Virtual axes of the passes for the grid and S surfaces (VLayout): a grid
+// axis longer than a pass line (DSO_MAX_LINE), or an axis 0 whose S surfaces
+// do not fit the potential pass's tile (S n > 8192), is split into
+// n1 = 2^floor(log2(n) / 2) and n2 = n / n1 (both <= 2048 for n <= 2^22, so
+// S n1 <= 8192 for every S <= 4).
+void plan_virtual(dso_ctx* c) {
+  c->Dv = 0;
+  for (int d = 0; d < c->D; ++d) {
+    const int64_t n = c->n[d];
+    if (n > DSO_MAX_LINE || (d == 0 && (long long)c->S * n > 8192)) {
+      const int64_t n1 = 1LL << (ilog2(n) / 2);
+      c->nv[c->Dv] = n1;
+      c->vpart[c->Dv++] = 1;
+      c->nv[c->Dv] = n / n1;
+      c->vpart[c->Dv++] = 2;
+    } else {
+      c->nv[c->Dv] = n;
+      c->vpart[c->Dv++] = 0;
+    }
+  }
 }
+
+VLayout vlayout(const dso_ctx* c) {
+  VLayout v{};
+  v.Dv = c->Dv;
+  for (int a = 0; a < DSO_MAX_VAXES; ++a) {
+    v.nv[a] = a < c->Dv ? c->nv[a] : 1;
+    v.part[a] = a < c->Dv ? c->vpart[a] : 0;
+  }
+  v.D = c->D;
+  for (int d = 0; d < 3; ++d) v.n[d] = c->n[d];
+  return v;
+}
+
+// Line length of the passes along virtual axis d.
+int kind_L(const dso_ctx* c, int d, int /*which*/) { return (int)c->nv[d]; }
 
 // Tile lines per surface for a pass over lines of length L staging SV
 // surfaces: the largest power of two giving at most about 128 threads
@@ -254,7 +284,7 @@ bool encode_view(CUtensorMap* m, const void* base, long long P, int L, long long
 }
 
 cudaError_t run_pass(dso_ctx* c, const Pass& p) {
-  const int L = p.L ? p.L : (int)c->n[p.axis];
+  const int L = (int)c->nv[p.axis];
   PassArgs a{};  // every field defined; the kernels read all of them
   const size_t es = c->esz();
   a.psi = c->psi;
@@ -269,13 +299,22 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   if (!a.tw) return cudaErrorInvalidValue;  // no twiddle table for this line length
   a.P = c->P;
   long long stride = 1;
-  for (int d = p.axis + 1; d < c->D; ++d) stride *= c->n[d];
+  for (int d = p.axis + 1; d < c->Dv; ++d) stride *= c->nv[d];
   a.stride = stride;
   a.lines = c->P / L;
   a.S = c->S;
   const int which = p.SV == 1 ? 0 : 1;
   a.G = c->G[p.axis][which];
   a.flags = p.flags;
+  if (c->vpart[p.axis] == 1 && (p.flags & (PASS_INV_FIRST | PASS_FWD))) {
+    // FFTs along the first factor of a split axis carry the four-step twiddles
+    if (p.flags & PASS_T) return cudaErrorInvalidConfiguration;  // never planned
+    a.flags |= PASS_XTW;
+    a.xtw = c->xtw[p.axis];
+    a.xtw_n2_log2 = ilog2(c->nv[p.axis + 1]);
+    a.xtw_s2_log2 = ilog2(stride / c->nv[p.axis + 1]);
+    if (!a.xtw) return cudaErrorInvalidValue;
+  }
   if (a.G < 1 || (a.G & (a.G - 1)) || a.lines % a.G) return cudaErrorInvalidConfiguration;
   a.stride_log2 = ilog2(stride);
   a.G_log2 = ilog2(a.G);
@@ -341,7 +380,7 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
 // TVT, D = 1:   [F0 T I0], then [V F0 T I0] per substep; the final pass is
 //   [V F0 T I0] with the step's last coefficients.
 void t_action(const dso_ctx* c, std::vector<Pass>& out, bool standalone_f0, int tb, int tb2) {
-  const int D = c->D;
+  const int D = c->Dv;
   if (standalone_f0) out.push_back(mkpass(0, 1, PASS_FWD));
   for (int d = 1; d <= D - 2; ++d) out.push_back(mkpass(d, 1, PASS_FWD));
   out.push_back(mkpass(D - 1, 1, PASS_FWD | PASS_T, -1, -1, tb, tb2));
@@ -354,20 +393,13 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
   const std::vector<int>& ib = c->coeffs.ib;
   const int NB = (int)c->coeffs.b.size();
   const int last = (int)c->coeffs.a.size() - 1;  // = NB
-  const int D = c->D;
+  const int D = c->Dv;
   if (c->elementary == DSO_VTV) {
     for (int j = 0; j < NB; ++j) {
       int u1 = ia[j], u2 = -1;
       if (j == 0 && !first) {
         u1 = ia[last];
         u2 = ia[0];
-      }
-      if (D == 1 && split_1d(c)) {
-        Pass v = mkpass(0, c->S, 0, u1, u2);
-        v.L = kVLine;
-        out.push_back(v);
-        out.push_back(mkpass(0, 1, PASS_FWD | PASS_T, -1, -1, ib[j]));
-        continue;
       }
       if (D == 1) {
         out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, u1, u2, ib[j]));
@@ -384,15 +416,6 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
     const int tb = (j == 0 && !first) ? ia[last] : ia[j];
     const int tb2 = (j == 0 && !first) ? ia[0] : -1;
     const int uv = (j == 0) ? (first ? -1 : ib[NB - 1]) : ib[j - 1];
-    if (D == 1 && split_1d(c)) {
-      if (uv >= 0) {
-        Pass v = mkpass(0, c->S, 0, uv);
-        v.L = kVLine;
-        out.push_back(v);
-      }
-      out.push_back(mkpass(0, 1, PASS_FWD | PASS_T, -1, -1, tb, tb2));
-      continue;
-    }
     if (D == 1) {
       out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, tb, tb2));
       continue;
@@ -408,20 +431,11 @@ std::vector<Pass> final_passes(const dso_ctx* c) {
   const int last = (int)c->coeffs.a.size() - 1;
   const int NB = (int)c->coeffs.b.size();
   if (c->elementary == DSO_VTV) {
-    Pass v = mkpass(0, c->S, c->D == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last]);
-    if (split_1d(c)) v.L = kVLine;
-    out.push_back(v);
+    out.push_back(mkpass(0, c->S, c->Dv == 1 ? 0 : PASS_INV_FIRST, c->coeffs.ia[last]));
     return out;
   }
   const int uv = c->coeffs.ib[NB - 1];
-  if (split_1d(c)) {
-    Pass v = mkpass(0, c->S, 0, uv);
-    v.L = kVLine;
-    out.push_back(v);
-    out.push_back(mkpass(0, 1, PASS_FWD | PASS_T, -1, -1, c->coeffs.ia[last]));
-    return out;
-  }
-  if (c->D == 1) {
+  if (c->Dv == 1) {
     out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, c->coeffs.ia[last]));
     return out;
   }
@@ -440,12 +454,17 @@ std::vector<Pass> final_passes(const dso_ctx* c) {
   } while (0)
 
 dso_status ensure_twiddles(dso_ctx* c) {
-  // every line length a pass uses: the axis lengths, and the view of the
-  // pointwise potential pass of a long 1-D grid (the persistent and TMA
-  // kernels stage the twiddles of their line length even when they do no FFT)
+  // the FFT twiddles of every line length a pass uses (the virtual axis
+  // lengths), and the four-step twiddles of every split axis
   std::vector<int> lens;
-  for (int d = 0; d < c->D; ++d) lens.push_back((int)c->n[d]);
-  if (split_1d(c)) lens.push_back(kVLine);
+  for (int d = 0; d < c->Dv; ++d) lens.push_back((int)c->nv[d]);
+  for (int d = 0; d + 1 < c->Dv; ++d) {
+    if (c->vpart[d] != 1 || c->xtw[d]) continue;
+    const int64_t n = c->nv[d] * c->nv[d + 1];
+    CK(cudaMalloc(&c->xtw[d], (size_t)n * c->esz()));
+    CK(launch_split_twiddles(c->xtw[d], c->prec == DSO_FP32, c->nv[d], c->nv[d + 1], c->stream));
+    c->launches += 1;
+  }
   for (int L : lens) {
     const int l = ilog2(L);
     if (c->tw[l]) continue;
@@ -490,13 +509,14 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
                                c->V + (size_t)b * NP * c->P, c->tau_a, na, c->S, c->P, c->stream));
     c->launches += 1;
   }
-  std::vector<double2> fac = host_kinetic_factors(c->D, c->n, c->qmin, c->qmax, c->mass, tco, dt);
-  double2* dfac = nullptr;
-  CK(cudaMalloc(&dfac, fac.size() * sizeof(double2)));
-  cudaError_t e = cudaMemcpyAsync(dfac, fac.data(), fac.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = launch_kinetic_tables(c->tau, c->prec == DSO_FP32, dfac, nb, c->D, c->n, c->P, c->stream);
+  std::vector<double> coef = host_kinetic_coefficients(c->D, c->qmin, c->qmax, c->mass, tco, dt);
+  double* dcoef = nullptr;
+  CK(cudaMalloc(&dcoef, coef.size() * sizeof(double)));
+  cudaError_t e = cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess) e = launch_kinetic_tables(c->tau, c->prec == DSO_FP32, dcoef, nb, vlayout(c), c->P, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(dfac);
+  cudaFree(dcoef);
   CK(e);
   c->launches += 1;
   c->tables_valid = true;
@@ -515,9 +535,9 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 // stream of jobs of one shape (a serving loop) tunes once.
 using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int>;
 struct TuneVal {
-  int G[DSO_MAX_DIM][2];
-  int variant[DSO_MAX_DIM][2];
-  int cps[DSO_MAX_DIM][2];
+  int G[DSO_MAX_VAXES][2];
+  int variant[DSO_MAX_VAXES][2];
+  int cps[DSO_MAX_VAXES][2];
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -535,13 +555,14 @@ dso_status autotune_tiles(dso_ctx* c) {
     int d, w, v, g, cp, used;
     while (sscanf(q, "%d,%d,%d,%d,%d;%n", &d, &w, &v, &g, &cp, &used) == 5) {
       q += used;
-      if (d < 0 || d >= c->D || w < 0 || w > 1 || v < 0 || v > 3 || g < 1 || (g & (g - 1))) continue;
+      if (d < 0 || d >= c->Dv || w < 0 || w > 1 || v < 0 || v > 3 || g < 1 || (g & (g - 1))) continue;
+      if (c->vpart[d] == 1 && v != 0) continue;  // split-axis twiddles: tile kernel only
       const long long L = kind_L(c, d, w), lines = c->P / L;
       const int SV = w ? c->S : 1;
       if (g > axis_pass_max_tile_lines((int)L, SV) || lines % g) continue;
       if (c->prec == DSO_FP32 && v != 0) continue;
       if ((v == 1 && !axis_pass_pq_supported((int)L, SV, g)) || (v == 2 && !axis_pass_tma_supported((int)L, SV, g)) ||
-          (v == 3 && (!axis_pass_tmap_supported((int)L, SV, g) || c->D == 1)))
+          (v == 3 && (!axis_pass_tmap_supported((int)L, SV, g) || c->Dv == 1)))
         continue;
       c->G[d][w] = g;
       c->variant[d][w] = v;
@@ -582,7 +603,7 @@ dso_status autotune_tiles(dso_ctx* c) {
   for (const Pass& q : step_passes(c, false)) plan.push_back(q);
   for (const Pass& q : final_passes(c)) plan.push_back(q);
   std::vector<Pass> reps;
-  bool both[DSO_MAX_DIM][2] = {};  // some pass of the kind applies a potential and a kinetic phase (1-D)
+  bool both[DSO_MAX_VAXES][2] = {};  // some pass of the kind applies a potential and a kinetic phase (1-D)
   for (const Pass& q : plan)
     if (q.u1 >= 0 && q.tb >= 0) both[q.axis][q.SV == 1 ? 0 : 1] = true;
   for (const Pass& q : plan) {
@@ -757,12 +778,15 @@ void dso_destroy(dso_ctx* c) {
 dso_status dso_set_grid(dso_ctx* c, int D, const int64_t* n, const double* qmin, const double* qmax) {
   if (!c || !n || !qmin || !qmax) return fail(DSO_EINVAL, "null argument");
   if (D < 1 || D > DSO_MAX_DIM) return fail(DSO_EINVAL, "D must be 1..3");
+  long long P = 1;
   for (int d = 0; d < D; ++d) {
-    if (!is_pow2(n[d]) || n[d] < DSO_MIN_AXIS || n[d] > (D == 1 ? DSO_MAX_AXIS_1D : DSO_MAX_AXIS))
-      return fail(DSO_EINVAL, "each n[d] must be a power of two in [8, 4096] (a 1-D grid up to 8192)");
+    if (!is_pow2(n[d]) || n[d] < DSO_MIN_AXIS || n[d] > DSO_MAX_AXIS)
+      return fail(DSO_EINVAL, "each n[d] must be a power of two in [8, 2^22]");
     if (!std::isfinite(qmin[d]) || !std::isfinite(qmax[d]) || !(qmax[d] > qmin[d]))
       return fail(DSO_EINVAL, "need finite qmin < qmax on every axis");
+    P *= n[d];
   }
+  if (P > DSO_MAX_POINTS) return fail(DSO_EINVAL, "the grid may have at most 2^30 points per surface");
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   drop_model(c);
@@ -810,16 +834,6 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   if (!c->have_grid) return fail(DSO_ESTATE, "grid not set");
   if (S < 2 || S > DSO_MAX_SURFACES) return fail(DSO_EINVAL, "S must be 2..4");
   if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
-  if (c->D == 1) {
-    // lines of S * n <= 8192 points fuse the potential with the FFT pass;
-    // longer ones (up to 8192 points per surface) run it as its own pass
-    if (!axis_pass_supported((int)c->n[0], 1))
-      return fail(DSO_EINVAL, "1-D grid too long (n must be <= 8192)");
-  } else {
-    for (int d = 0; d < c->D; ++d)
-      if (!axis_pass_supported((int)c->n[d], d == 0 ? S : 1))
-        return fail(DSO_EINVAL, "axis length too long for this surface count (S * n[0] must be <= 8192)");
-  }
   const size_t count = (size_t)c->B * (S * (S + 1) / 2) * c->P;
   if (where == DSO_HOST) {
     for (size_t i = 0; i < count; ++i)
@@ -865,9 +879,16 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
     CK(cudaMemsetAsync(c->err, 0, 16 * sizeof(int), c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
-  for (int d = 0; d < c->D; ++d) {
-    c->G[d][0] = choose_G(c, (int)c->n[d], 1);
-    c->G[d][1] = choose_G(c, (d == 0 && split_1d(c)) ? kVLine : (int)c->n[d], S);
+  plan_virtual(c);
+  for (int d = 0; d < c->Dv; ++d) {
+    // every pass line fits one tile: S surfaces of a virtual axis-0 line,
+    // one surface of any other
+    if (!axis_pass_supported((int)c->nv[d], d == 0 ? S : 1)) {
+      drop_model(c);
+      return fail(DSO_EINVAL, "internal: a pass line does not fit a tile");
+    }
+    c->G[d][0] = choose_G(c, (int)c->nv[d], 1);
+    c->G[d][1] = choose_G(c, (int)c->nv[d], S);
     c->variant[d][0] = c->variant[d][1] = 0;
   }
   c->have_V = true;
@@ -1191,7 +1212,7 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
   void* keep = c->psi;
   c->psi = c->work;
   cudaError_t e = cudaSuccess;
-  for (int d = 0; d < c->D && e == cudaSuccess; ++d) e = run_pass(c, mkpass(d, 1, PASS_FWD));
+  for (int d = 0; d < c->Dv && e == cudaSuccess; ++d) e = run_pass(c, mkpass(d, 1, PASS_FWD));
   c->psi = keep;
   CK(e);
   const int NPV = c->S * (c->S + 1) / 2;
@@ -1202,8 +1223,7 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
     a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
     a.V = c->V + (size_t)b * NPV * c->P;
     a.Tax = c->Tax;
-    for (int d = 0; d < 3; ++d) a.n[d] = c->n[d];
-    a.D = c->D;
+    a.vl = vlayout(c);
     a.S = c->S;
     a.P = c->P;
     CK(launch_observables(a, c->partials, c->obs_out + (size_t)b * DSO_OBS_COLS, c->stream));
@@ -1336,7 +1356,7 @@ int64_t dso_launch_count(const dso_ctx* c) { return c ? c->launches : 0; }
 int dso_tuned_plan(const dso_ctx* c, char* out, int cap) {
   if (!c || !out || cap < 1) return fail(DSO_EINVAL, "dso_tuned_plan: null argument");
   std::string s;
-  for (int d = 0; d < c->D; ++d)
+  for (int d = 0; d < c->Dv; ++d)
     for (int w = 0; w < 2; ++w) {
       char e[64];
       snprintf(e, sizeof(e), "%d,%d,%d,%d,%d;", d, w, c->variant[d][w], c->G[d][w], c->cps[d][w]);
@@ -1354,7 +1374,7 @@ const char* dso_last_error(void) { return g_err.c_str(); }
 namespace dso {
 
 bool axis_pass_supported(int L, int SV) {
-  if (L < 8 || L > 8192 || (L & (L - 1))) return false;
+  if (L < 8 || L > DSO_MAX_LINE || (L & (L - 1))) return false;
   if (SV < 1 || SV > 4) return false;
   return (long long)SV * L <= 8192;
 }

@@ -15,6 +15,46 @@
 
 namespace dso {
 
+// Virtual axes of the passes.  A pass transforms whole lines of one axis held
+// in shared memory, which bounds a line's length (4096 points, and S x 8192
+// for the potential pass that stages all S surfaces of an axis-0 line).  A
+// longer grid axis of n points is viewed as two axes, index i1 * n2 + i2 with
+// n = n1 * n2, and transformed in four steps: FFTs of length n1 along i1, a
+// twiddle multiplication by w_n^(k1 i2), FFTs of length n2 along i2 (the
+// Cooley-Tukey splitting behind the FFTs of Sec. II G).  Frequency
+// k1 + n1 k2 then sits at storage position (k1, k2): the momentum
+// representation is stored permuted along a split axis, which only the
+// kinetic phases and <T> need to know.
+#define DSO_MAX_VAXES 6
+#define DSO_MAX_LINE 4096  // longest line of a pass
+#define DSO_MAX_GRID_AXIS (1 << 22)
+struct VLayout {
+  int Dv;                       // virtual axes (row-major, last contiguous)
+  int64_t nv[DSO_MAX_VAXES];    // their lengths
+  int part[DSO_MAX_VAXES];      // 0: a whole grid axis, 1: first factor (n1) of a split one, 2: second (n2)
+  int D;                        // grid axes
+  int64_t n[3];                 // grid axis lengths
+};
+
+// Momentum index along every grid axis of storage position g of the
+// momentum representation (after forward FFTs along every virtual axis).
+__host__ __device__ inline void momentum_indices(const VLayout& v, long long g, int64_t (&k)[3]) {
+  int64_t kv[DSO_MAX_VAXES];
+  for (int a = v.Dv - 1; a >= 0; --a) {
+    kv[a] = g & (v.nv[a] - 1);  // lengths are powers of two
+    g /= v.nv[a];
+  }
+  int d = 0;
+  for (int a = 0; a < v.Dv; ++a) {
+    if (v.part[a] == 1) {
+      k[d++] = kv[a] + v.nv[a] * kv[a + 1];
+      ++a;
+    } else {
+      k[d++] = kv[a];
+    }
+  }
+}
+
 // Pruned splitting coefficients of one composed scheme (Sec. II D-F).
 struct Coeffs {
   std::vector<double> a, b;          // a~ (N_B + 1 entries), b~ (N_B entries)
@@ -60,15 +100,23 @@ cudaError_t launch_axis_pass_sv4(int L, int variant, const PassArgs& a, long lon
 // rounded once (a zero cosine is replaced by 2^-500, or 2^-60 for the FP32
 // table, so that the tangent stays finite).
 std::vector<double2> host_twiddles(int L, bool fp32);
-// Kinetic phase factors per axis: for each unique b (nb of them), the
-// D 1-D factor tables exp(-i b dt p_k^2 / (2 m_d)) concatenated over axes
-// (sum n_d entries), 1/P folded into axis 0.  Host long double.
-std::vector<double2> host_kinetic_factors(int D, const int64_t* n, const double* qmin, const double* qmax,
-                                          const double* mass, const std::vector<double>& b_unq, double dt);
-// tau[u][g] = prod_d factor_d(u, k_d(g)) on the device.
-// Output is double2, or float2 rounded from the FP64 product when fp32.
-cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double2* factors, int nb, int D, const int64_t* n,
-                                  long long P, cudaStream_t st);
+// Kinetic phase coefficients: the phase of unique b (nb of them) at momentum
+// index kk_d (folded to [-n_d/2, n_d/2)) is sum_d C[u][d] kk_d^2 with
+// C = -b dt (2 pi / extent_d)^2 / (2 m_d), computed on the host in long double
+// and passed as an unevaluated sum hi + lo of two doubles per (u, d):
+// coef[(u * D + d) * 2 + {0, 1}].
+std::vector<double> host_kinetic_coefficients(int D, const double* qmin, const double* qmax, const double* mass,
+                                              const std::vector<double>& b_unq, double dt);
+// tau[u][g] = exp(i phase_u(k(g))) / P at every storage position g of the
+// momentum representation (momentum_indices), the phase summed in
+// double-double and exponentiated with one sincos plus a first-order
+// correction for the low part.  Output is double2, or float2 rounded once.
+cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double* coef, int nb, const VLayout& v, long long P,
+                                  cudaStream_t st);
+// Twiddles of a split axis of n = n1 * n2 points: xtw[k1 * n2 + i2] =
+// exp(-2 pi i (k1 i2 mod n) / n) (sincospi of an exact argument), double2
+// or rounded once to float2.
+cudaError_t launch_split_twiddles(void* xtw, bool fp32, int64_t n1, int64_t n2, cudaStream_t st);
 // U[u][k][g] = exp(-i a_u dt V(q_g)) packed upper, for every unique a.
 // FP64 throughout; stored as double2, or rounded once to float2 when fp32.
 cudaError_t launch_potential_tables(void* U, bool fp32, const double* V, const double* tau_a, int na, int S,
@@ -78,11 +126,11 @@ cudaError_t launch_potential_tables(void* U, bool fp32, const double* V, const d
 // final reduction.  `spec` holds |psi~|^2-weighting per axis (p^2 / 2m).
 struct ObsArgs {
   const void* psi;        // position representation [S][P] (double2, or float2 when fp32)
-  const void* psik;       // momentum representation [S][P] (unnormalised FFT)
+  const void* psik;       // momentum representation [S][P] (unnormalised FFT, storage order of vl)
   const double* V;        // packed potential [S(S+1)/2][P]
-  const double* Tax;      // concatenated per-axis p_k^2/(2 m_d)
-  int64_t n[3];
-  int D, S;
+  const double* Tax;      // concatenated per-axis p_k^2/(2 m_d), natural momentum order
+  VLayout vl;             // storage order of psik
+  int S;
   long long P;
   int fp32;
 };

@@ -58,19 +58,15 @@ __global__ void obs_partial_kernel(ObsArgs a, double* __restrict__ partials) {
         ++k;
       }
     acc[a.S] += ev;
-    // kinetic weight of this momentum grid point
-    long long rem = g;
+    // kinetic weight of this momentum grid point (storage order of a.vl:
+    // permuted along split axes)
+    int64_t kd[3] = {0, 0, 0};
+    momentum_indices(a.vl, g, kd);
     double T = 0.0;
     int64_t off = 0;
-    int64_t offs[3];
-    for (int d = 0; d < a.D; ++d) {
-      offs[d] = off;
-      off += a.n[d];
-    }
-    for (int d = a.D - 1; d >= 0; --d) {
-      const int64_t kd = rem % a.n[d];
-      rem /= a.n[d];
-      T += a.Tax[offs[d] + kd];
+    for (int d = 0; d < a.vl.D; ++d) {
+      T += a.Tax[off + kd[d]];
+      off += a.vl.n[d];
     }
     double m2 = 0.0;
     for (int s = 0; s < a.S; ++s) {

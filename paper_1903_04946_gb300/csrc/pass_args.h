@@ -9,6 +9,8 @@ enum PassFlags : int {
   PASS_INV_FIRST = 1,  // inverse FFT before the potential step
   PASS_FWD = 2,        // forward FFT after the potential step
   PASS_T = 4,          // kinetic phase then inverse FFT after the forward FFT
+  PASS_XTW = 8,        // the axis is the first factor of a split axis: conj twiddles
+                       // before the inverse FFT, twiddles after the forward FFT
 };
 
 // Complex arrays are double2 (FP64 path) or float2 (FP32 storage mode).
@@ -42,6 +44,9 @@ struct PassArgs {
   int dec0;                // surface 0 uncoupled (block-diagonal potential): skip its zero products
   int ctas_per_sm;         // host side, persistent variants: resident CTAs per SM (0: as many as fit)
   int pdl;                 // host side: launch with programmatic dependent launch
+  const void* xtw;         // PASS_XTW: split-axis twiddles [n1][n2], w_n^(k1 i2), or null
+  int xtw_n2_log2;         // log2 n2 (length of the second factor of the split axis)
+  int xtw_s2_log2;         // log2 of the second factor's stride (product of the later axes)
 };
 
 // Tile index -> (first staged surface over all jobs, job).  A pass staging

@@ -144,6 +144,7 @@ template <int L, int SV>
 cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, unsigned* queue, const TmaMaps* maps,
                            cudaStream_t st) {
   if (variant != 0 && a.fp32) return cudaErrorInvalidConfiguration;  // FP64 only
+  if (variant != 0 && (a.flags & PASS_XTW)) return cudaErrorInvalidConfiguration;  // split axes: tile kernel
   if (variant == 1) {
     if constexpr (SV * L / 8 <= 256) return launch_pq<L, SV>(a, ntiles, queue, st);
     return cudaErrorInvalidConfiguration;
@@ -176,9 +177,6 @@ cudaError_t launch_by_length(int L, int variant, const PassArgs& a, long long nt
       break;
     case 4096:
       if constexpr (SV * 4096 <= 8192) return launch_variant<4096, SV>(variant, a, ntiles, queue, maps, st);
-      break;
-    case 8192:  // 1-D grids only, one surface per line
-      if constexpr (SV == 1) return launch_variant<8192, SV>(variant, a, ntiles, queue, maps, st);
       break;
     default: break;
   }

@@ -7,9 +7,11 @@
 //   * FFT twiddles exp(-2 pi i m / L) in tangent form (cos, tan), host long
 //     double;
 //   * kinetic phases tau_b(p) = exp(-i b dt T(p)) / P with
-//     T(p) = sum_d p_d^2 / (2 m_d) (Eq. (diab_mol_ham)), as a product of 1-D
-//     factors computed on the host in long double (the 1/P of the unnormalised
-//     inverse FFT is an exact power of two folded into axis 0);
+//     T(p) = sum_d p_d^2 / (2 m_d) (Eq. (diab_mol_ham)): the phase from
+//     long-double coefficients, accumulated in double-double on the device
+//     and exponentiated once (the 1/P of the unnormalised inverse FFTs is an
+//     exact power of two);
+//   * twiddles of split (long) axes for the four-step FFT;
 //   * potential unitaries U_a(q) = exp(-i a dt V(q)) (Sec. II H): for S = 2 the
 //     closed form that one Jacobi rotation gives; for S >= 3 cyclic Jacobi to
 //     convergence, then U = W diag(exp(-i a dt lambda)) W^T.  Stored packed
@@ -36,28 +38,18 @@ std::vector<double2> host_twiddles(int L, bool fp32) {
   return tw;
 }
 
-std::vector<double2> host_kinetic_factors(int D, const int64_t* n, const double* qmin, const double* qmax,
-                                          const double* mass, const std::vector<double>& b_unq, double dt) {
-  int64_t tot = 0, P = 1;
-  for (int d = 0; d < D; ++d) {
-    tot += n[d];
-    P *= n[d];
-  }
+std::vector<double> host_kinetic_coefficients(int D, const double* qmin, const double* qmax, const double* mass,
+                                              const std::vector<double>& b_unq, double dt) {
   const long double two_pi = 6.283185307179586476925286766559005768L;
-  std::vector<double2> out((size_t)tot * b_unq.size());
+  std::vector<double> out(b_unq.size() * (size_t)D * 2);
   for (size_t u = 0; u < b_unq.size(); ++u) {
     const long double tb = (long double)b_unq[u] * (long double)dt;
-    int64_t off = 0;
     for (int d = 0; d < D; ++d) {
-      const long double extent = (long double)qmax[d] - (long double)qmin[d];
-      const long double scale = (d == 0) ? 1.0L / (long double)P : 1.0L;
-      for (int64_t k = 0; k < n[d]; ++k) {
-        const int64_t kk = (k < n[d] / 2) ? k : k - n[d];
-        const long double p = two_pi * (long double)kk / extent;  // 2 pi k / (n dq)
-        const long double ang = -tb * p * p / (2.0L * (long double)mass[d]);
-        out[u * tot + off + k] = make_double2((double)(scale * cosl(ang)), (double)(scale * sinl(ang)));
-      }
-      off += n[d];
+      const long double w = two_pi / ((long double)qmax[d] - (long double)qmin[d]);  // 2 pi / (n dq)
+      const long double C = -tb * w * w / (2.0L * (long double)mass[d]);
+      const double hi = (double)C;
+      out[(u * D + d) * 2] = hi;
+      out[(u * D + d) * 2 + 1] = (double)(C - (long double)hi);
     }
   }
   return out;
@@ -66,40 +58,72 @@ std::vector<double2> host_kinetic_factors(int D, const int64_t* n, const double*
 __device__ __forceinline__ void store_c(double2* p, double x, double y) { *p = make_double2(x, y); }
 __device__ __forceinline__ void store_c(float2* p, double x, double y) { *p = make_float2((float)x, (float)y); }
 
+// tau[u][g]: the kinetic phase of every unique b at storage position g.  The
+// angle sum_d C_d kk_d^2 is accumulated as hi + lo (kk_d^2 < 2^42 is exact;
+// fma gives the exact error of each product, Knuth's two-sum that of each
+// addition), so it carries the long-double coefficients to about 1e-30
+// relative; exp(i (hi + lo)) = (cos hi + i sin hi)(1 + i lo) to first order
+// in |lo| <= a few ulp of hi.
 template <typename OutC>
-__global__ void kinetic_table_kernel(OutC* __restrict__ tau, const double2* __restrict__ fac, int nb, int D,
-                                     int64_t n0, int64_t n1, int64_t n2, long long P) {
+__global__ void kinetic_table_kernel(OutC* __restrict__ tau, const double* __restrict__ coef, int nb, VLayout v,
+                                     long long P, double inv_P) {
   const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (g >= P) return;
   const int u = blockIdx.y;
-  const int64_t tot = n0 + (D > 1 ? n1 : 0) + (D > 2 ? n2 : 0);
-  const double2* f = fac + (size_t)u * tot;
-  int64_t k[3];
-  long long r = g;
-  const int64_t nn[3] = {n0, n1, n2};
-  for (int d = D - 1; d >= 0; --d) {
-    k[d] = r % nn[d];
-    r /= nn[d];
+  int64_t k[3] = {0, 0, 0};
+  momentum_indices(v, g, k);
+  double hi = 0.0, lo = 0.0;
+  for (int d = 0; d < v.D; ++d) {
+    const int64_t kk = (k[d] < v.n[d] / 2) ? k[d] : k[d] - v.n[d];
+    const double x = (double)(kk * kk);
+    const double ch = coef[(u * v.D + d) * 2], cl = coef[(u * v.D + d) * 2 + 1];
+    const double p = ch * x;
+    const double pe = fma(ch, x, -p);  // exact error of the product
+    const double s = hi + p;           // two-sum
+    const double bb = s - hi;
+    const double se = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += se + pe + cl * x;
   }
-  double2 t = f[k[0]];
-  int64_t off = n0;
-  for (int d = 1; d < D; ++d) {
-    const double2 x = f[off + k[d]];
-    t = make_double2(t.x * x.x - t.y * x.y, t.x * x.y + t.y * x.x);
-    off += nn[d];
-  }
-  store_c(&tau[(size_t)u * P + g], t.x, t.y);
+  const double r = hi + lo;  // renormalise
+  lo = lo - (r - hi);
+  hi = r;
+  double sn, cs;
+  sincos(hi, &sn, &cs);
+  store_c(&tau[(size_t)u * P + g], inv_P * (cs - sn * lo), inv_P * (sn + cs * lo));
 }
 
-cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double2* factors, int nb, int D, const int64_t* n,
-                                  long long P, cudaStream_t st) {
+cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double* coef, int nb, const VLayout& v, long long P,
+                                  cudaStream_t st) {
   dim3 grid((unsigned)((P + 255) / 256), (unsigned)nb);
+  const double inv_P = 1.0 / (double)P;  // a power of two: exact
   if (fp32)
-    kinetic_table_kernel<<<grid, 256, 0, st>>>((float2*)tau, factors, nb, D, n[0], D > 1 ? n[1] : 1,
-                                               D > 2 ? n[2] : 1, P);
+    kinetic_table_kernel<<<grid, 256, 0, st>>>((float2*)tau, coef, nb, v, P, inv_P);
   else
-    kinetic_table_kernel<<<grid, 256, 0, st>>>((double2*)tau, factors, nb, D, n[0], D > 1 ? n[1] : 1,
-                                               D > 2 ? n[2] : 1, P);
+    kinetic_table_kernel<<<grid, 256, 0, st>>>((double2*)tau, coef, nb, v, P, inv_P);
+  return cudaGetLastError();
+}
+
+// Split-axis twiddles w_n^(k1 i2) in the [n1][n2] layout of the passes.
+template <typename OutC>
+__global__ void split_twiddle_kernel(OutC* __restrict__ xtw, int64_t n1, int64_t n2) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = n1 * n2;
+  if (idx >= n) return;
+  const long long k1 = idx / n2, i2 = idx - k1 * n2;
+  const long long m = (k1 * i2) & (n - 1);
+  double sn, cs;
+  sincospi(-2.0 * (double)m / (double)n, &sn, &cs);  // m / n is exact (n a power of two)
+  store_c(&xtw[idx], cs, sn);
+}
+
+cudaError_t launch_split_twiddles(void* xtw, bool fp32, int64_t n1, int64_t n2, cudaStream_t st) {
+  const long long n = n1 * n2;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (fp32)
+    split_twiddle_kernel<<<blocks, 256, 0, st>>>((float2*)xtw, n1, n2);
+  else
+    split_twiddle_kernel<<<blocks, 256, 0, st>>>((double2*)xtw, n1, n2);
   return cudaGetLastError();
 }
 

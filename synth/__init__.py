@@ -272,32 +272,26 @@ SERVING_DT = {2: 2.0, 4: 10.0, 6: 20.0, 8: 40.0}
 
 
 def serving_job(seed: int, max_points: int = 1 << 21, min_points: int = 1 << 8):
-    """One seeded propagation request: D in {1, 2, 3}, a power-of-two grid with
-    min_points..max_points points per surface (each axis 8..4096 points and
-    S * n_0 <= 8192), S in {2, 3, 4} surfaces with harmonic diagonals in
-    dimensionless normal coordinates (omega ~ U[0.005, 0.02], m = 1/omega)
-    plus seeded linear couplings, a displaced Gaussian on surface 1, order in
-    {2, 4, 6, 8} (triple jump), t ~ U[500, 5000] rounded to a multiple of
-    the order's dt (SERVING_DT).  Returns (problem, order, t, dt)."""
+    """One seeded propagation request of the serving workload: D in {1, 2, 3},
+    a power-of-two grid of min_points..max_points points per surface, S in
+    {2, 3, 4} surfaces with harmonic diagonals in dimensionless normal
+    coordinates (omega ~ U[0.005, 0.02], m = 1/omega) plus seeded linear
+    couplings, a displaced Gaussian on surface 1, order in {2, 4, 6, 8}
+    (triple jump), t ~ U[500, 5000] rounded to a multiple of the order's dt
+    (SERVING_DT).  The grid's log2 size is drawn uniformly and its bits are
+    spread at random over the D axes, each axis keeping at least 8 points
+    (a D-dimensional grid therefore has at least 2^(3D) points).  Nothing is
+    redrawn to fit an implementation: any axis length up to the full size
+    can come out.  Returns (problem, order, t, dt)."""
     rng = np.random.default_rng(seed)
-    while True:
-        D = int(rng.integers(1, 4))
-        S = int(rng.integers(2, 5))
-        logp = int(rng.integers(int(np.log2(min_points)), int(np.log2(max_points)) + 1))
-        # split logp over D axes, each axis 2^3..2^12
-        parts = [3] * D
-        rest = logp - 3 * D
-        if rest < 0:
-            continue
-        for _ in range(rest):
-            cand = [i for i in range(D) if parts[i] < 12]
-            if not cand:
-                break
-            parts[int(rng.choice(cand))] += 1
-        n = tuple(2 ** p for p in parts)
-        if sum(parts) != logp or S * n[0] > 8192:
-            continue
-        break
+    D = int(rng.integers(1, 4))
+    S = int(rng.integers(2, 5))
+    lo = max(int(np.log2(min_points)), 3 * D)
+    logp = int(rng.integers(lo, max(lo, int(np.log2(max_points))) + 1))
+    parts = [3] * D
+    for _ in range(logp - 3 * D):
+        parts[int(rng.integers(0, D))] += 1
+    n = tuple(2 ** p for p in parts)
     omega = rng.uniform(0.005, 0.02, size=D)
     extent = 7.0
     qmin, qmax = tuple([-extent] * D), tuple([extent] * D)

@@ -154,13 +154,12 @@ def test_errors_are_reported(dso):
             dso.dso_set_psi(ctx, bad)
         assert ei.value.status == dso.DSO_ENUMERIC
         dso.dso_propagate(ctx, 0.0, 0.1)                   # zero steps: a no-op
-        dso.dso_set_grid(ctx, (4096, 8), (0.0, 0.0), (1.0, 1.0))
         with pytest.raises(dso.DSOError):
-            dso.dso_load_potential(ctx, 3, np.zeros((6, 4096, 8)))  # D >= 2 needs S * n[0] <= 8192
+            dso.dso_set_grid(ctx, (1 << 23,), (0.0,), (1.0,))      # axes up to 2^22 points
         with pytest.raises(dso.DSOError):
-            dso.dso_set_grid(ctx, (16384,), (0.0,), (1.0,))        # 1-D grids up to 8192
+            dso.dso_set_grid(ctx, (1 << 16, 1 << 15), (0.0, 0.0), (1.0, 1.0))  # at most 2^30 points
         with pytest.raises(dso.DSOError):
-            dso.dso_set_grid(ctx, (8192, 8), (0.0, 0.0), (1.0, 1.0))  # other axes up to 4096
+            dso.dso_set_grid(ctx, (4, 64), (0.0, 0.0), (1.0, 1.0))  # axes of at least 8 points
     finally:
         dso.dso_destroy(ctx)
 
@@ -193,7 +192,7 @@ def test_tvt_time_reversible_and_norm(dso):
     assert rel_l2(back, pr.psi0) < 1e-12
 
 
-# -- long 1-D grids (S * n > 8192): the potential step runs as its own pass
+# -- long 1-D grids (S * n > 8192): the axis is split into two virtual axes
 @pytest.mark.parametrize("N,S,el", [(8192, 2, "VTV"), (8192, 2, "TVT"), (4096, 3, "VTV"), (4096, 4, "TVT")])
 def test_long_1d_grids(dso, N, S, el):
     pr = synth.nai_like(seed=31, N=N) if S == 2 else synth.random_coupled(N + S, (N,), S, extent=40.0)

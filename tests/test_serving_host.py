@@ -16,7 +16,20 @@ def test_job_stream_reproducible_and_mixed():
     for j in a:
         assert abs(j.t / j.dt - round(j.t / j.dt)) < 1e-12
         assert 500 - j.dt <= j.t <= 5000 + j.dt
-        assert j.problem.S * j.problem.n[0] <= 8192 and all(8 <= x <= 4096 for x in j.problem.n)
+        assert all(x >= 8 for x in j.problem.n) and 2 ** 8 <= j.problem.points <= 2 ** 21
+
+
+def test_job_stream_spans_the_serving_configuration():
+    # D in {1, 2, 3}, 2^8..2^21 points per surface, S in {2, 3, 4}: the draw
+    # is not narrowed to any implementation limit (long axes included)
+    jobs = [synth.serving_job(1907 + i)[0] for i in range(200)]
+    assert {p.D for p in jobs} == {1, 2, 3}
+    assert {p.S for p in jobs} == {2, 3, 4}
+    logs = {int(np.log2(p.points)) for p in jobs}
+    assert min(logs) == 8 and max(logs) == 21
+    assert any(p.D == 1 and p.points > 8192 for p in jobs)
+    assert any(max(p.n) > 4096 for p in jobs if p.D >= 2)
+    assert any(p.S * p.n[0] > 8192 for p in jobs)
 
 
 def test_footprint_grows_with_grid_order_and_surfaces():
