@@ -55,7 +55,7 @@ typedef enum {
   DSO_ENOMEM = -2,   /* device allocation failed */
   DSO_ECUDA = -3,    /* CUDA runtime error */
   DSO_ESTATE = -4,   /* call out of order (e.g. propagate before set_psi) */
-  DSO_ETIMEOUT = -5, /* reserved: a bounded device wait gave up */
+  DSO_ETIMEOUT = -5, /* a bounded device wait gave up */
   DSO_ENUMERIC = -6  /* non-finite input or result */
 } dso_status;
 
@@ -157,6 +157,28 @@ dso_status dso_composition_coefficients(int m, const double* gamma, int* n_a, in
  * non-finite is DSO_EINVAL.  The paper has no counterpart. */
 dso_status dso_set_norm_check(dso_ctx* ctx, double tol);
 
+/* Diagnostics of the bounded device waits (failure detection).  The TMA
+ * kernel variants wait for their tile copies on mbarriers with a bounded
+ * number of polls; a wait that gives up lets every copy already started land,
+ * records a code, and the next synchronising call (dso_get_psi to host
+ * memory) returns DSO_ETIMEOUT.  With polls > 0, every tile of the TMA
+ * variant (variant 2 of dso_tuned_plan) additionally waits, with a limit of
+ * `polls`, on a barrier that no copy ever completes, so that the failure path
+ * can be exercised without a fault: the wait gives up, the timeout is
+ * reported, and the propagation itself is unaffected.  0 (the default)
+ * switches it off.  The paper has no counterpart. */
+dso_status dso_set_wait_probe(dso_ctx* ctx, int polls);
+
+/* Device address of the context's psi ([B][S][grid], the context's element
+ * type), borrowed: valid until a call that reallocates the state
+ * (dso_set_grid, dso_set_batch, dso_load_potential, dso_destroy).  Lets
+ * other device code read or write the state in place without a copy (for
+ * example dso_position_observables_noalloc).  Writes through it bypass the
+ * finite check of dso_set_psi and do not reset the norm monitor's reference,
+ * so dso_set_norm_check sees them as drift.  Work on another stream must be
+ * ordered with the context's stream by the caller. */
+dso_status dso_psi_device_pointer(dso_ctx* ctx, void** out);
+
 /* Set psi ([B][S][grid], complex128 or complex64 by the context's
  * precision) from host or device memory.  Host data is staged on the
  * device and checked there: a non-finite value returns DSO_ENUMERIC and
@@ -182,6 +204,27 @@ dso_status dso_get_psi(dso_ctx* ctx, void* out, int where);
  * Host arrays with one entry per job (norm, energy: B entries; pops: B*S,
  * job-major).  Any output pointer may be NULL.  Synchronises the stream. */
 dso_status dso_observables(dso_ctx* ctx, double* norm, double* energy, double* pops);
+
+/* Inner product of Sec. II A, <psi|phi> = dV sum_s sum_q conj(psi_s(q))
+ * phi_s(q), of the context's psi (the bra) with phi (the ket), per job: re[b]
+ * and im[b] (host arrays of B entries; either may be NULL).  The symplectic
+ * two-form is omega(psi, phi) = -2 im[b] (hbar = 1), and <psi|psi> is the
+ * squared norm.  phi has psi's layout and element type ([B][S][grid],
+ * complex128 or complex64 by the context's precision), in host memory
+ * (staged in the context's work buffer) or device memory (where).  The
+ * reduction is FP64 with fixed per-block partial sums added on the host in a
+ * fixed order, so the result does not depend on scheduling.  A propagation is
+ * unitary (Sec. II A, App. A): <U psi|U phi> = <psi|phi> to round-off.
+ * Synchronises the stream. */
+dso_status dso_inner(dso_ctx* ctx, const void* phi, int where, double* re, double* im);
+
+/* The phase of each surface's wavefunction at its density maximum (the
+ * wavepacket-phase observable of the convergence study, Sec. III A): for
+ * every job b and surface s, index[b*S+s] receives the first flat grid index
+ * (storage order) where |psi_s|^2 is largest and phase[b*S+s] = arg psi_s
+ * there, in (-pi, pi].  Host arrays of B*S entries; either may be NULL.
+ * Synchronises the stream. */
+dso_status dso_phase_at_density_maximum(dso_ctx* ctx, int64_t* index, double* phase);
 
 /* Pruned splitting coefficients of a composed scheme (Sec. II D-F), host
  * only (no context, no GPU): a~ has n_a = N_B + 1 entries and b~ n_b = N_B

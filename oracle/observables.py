@@ -1,7 +1,8 @@
 """Observables of a multi-surface wavepacket (oracle).
 
 Sec. II A defines the norm, the inner product, the symplectic two-form
-omega(psi, phi) = -2 hbar Im<psi|phi> and the energy <psi|H|psi>.  On the grid
+omega(psi, phi) = -2 hbar Im<psi|phi> and the energy <psi|H|psi>; Sec. III A
+also follows the phase of the wavepacket at its density maximum.  On the grid
 the inner product is <psi|phi> = sum_s sum_q conj(psi_s(q)) phi_s(q) dV with
 dV the product of the grid spacings.  <T> is evaluated in the momentum
 representation: with the unnormalised forward FFT, sum_q |psi|^2 =
@@ -51,6 +52,19 @@ def kinetic_energy(problem, psi) -> float:
 
 def energy(problem, psi) -> float:
     return kinetic_energy(problem, psi) + potential_energy(problem, psi)
+
+
+def phase_at_density_maximum(problem, psi):
+    """Phase of each surface's wavefunction where its density is largest
+    (the wavepacket-phase observable of the phase-convergence study, Sec.
+    III A; read as arg psi_s(q*) with q* the grid point of largest
+    |psi_s(q)|^2, the first such point in storage order on a tie).  Returns
+    (flat indices q*, phases in (-pi, pi]) per surface."""
+    S = psi.shape[0]
+    flat = psi.reshape(S, -1)
+    idx = np.argmax(np.abs(flat) ** 2, axis=1)
+    vals = flat[np.arange(S), idx]
+    return idx, np.angle(vals)
 
 
 def l2_error(problem, psi, ref) -> float:

@@ -27,7 +27,8 @@ EXPORTS = (
     "dso_set_scheme", "dso_set_psi", "dso_propagate", "dso_get_psi", "dso_observables",
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
     "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan", "dso_set_composition",
-    "dso_composition_coefficients", "dso_set_norm_check", "dso_fp64_issue_rate",
+    "dso_composition_coefficients", "dso_set_norm_check", "dso_fp64_issue_rate", "dso_inner",
+    "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer",
 )
 
 _lib = None
@@ -73,6 +74,10 @@ def load(path: str = LIB):
         "dso_last_error": (ctypes.c_char_p, []),
         "dso_position_observables_noalloc": (i32, [vp, vp, i32, i64, dbl, vp, vp]),
         "dso_fp64_issue_rate": (i32, [i32, pd]),
+        "dso_inner": (i32, [vp, vp, i32, pd, pd]),
+        "dso_phase_at_density_maximum": (i32, [vp, ctypes.POINTER(i64), pd]),
+        "dso_set_wait_probe": (i32, [vp, i32]),
+        "dso_psi_device_pointer": (i32, [vp, ctypes.POINTER(vp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -184,6 +189,26 @@ def dso_observables(ctx, S, B=1):
     return (np.array(norm[:]), np.array(energy[:]), np.array(pops[:], dtype=np.float64).reshape(B, S))
 
 
+def dso_inner(ctx, phi, B=1):
+    """<psi|phi> of the context's psi with phi (same layout and precision),
+    one complex number per job (a scalar when B == 1)."""
+    if isinstance(phi, np.ndarray):
+        phi = np.ascontiguousarray(phi)
+    p, where = _ptr(phi)
+    re, im = (ctypes.c_double * B)(), (ctypes.c_double * B)()
+    _check(load().dso_inner(ctx, p, where, re, im), "dso_inner")
+    out = np.array(re[:]) + 1j * np.array(im[:])
+    return complex(out[0]) if B == 1 else out
+
+
+def dso_phase_at_density_maximum(ctx, S, B=1):
+    """(flat indices, phases) of every job's surfaces at their density
+    maxima, arrays of B*S entries (job-major)."""
+    idx, ph = (ctypes.c_int64 * (B * S))(), (ctypes.c_double * (B * S))()
+    _check(load().dso_phase_at_density_maximum(ctx, idx, ph), "dso_phase_at_density_maximum")
+    return np.array(idx[:], dtype=np.int64), np.array(ph[:])
+
+
 def dso_scheme_coefficients(order, scheme=DSO_TRIPLE_JUMP):
     """(a~, b~, I^a, I^b, N_a^unq, N_b^unq) of a composed scheme (host only)."""
     lib = load()
@@ -248,6 +273,32 @@ def dso_composition_coefficients(gammas):
     _check(lib.dso_composition_coefficients(int(g.size), gp, None, None, a, b, ia, ib, None, None),
            "dso_composition_coefficients")
     return (np.array(a[:]), np.array(b[:]), np.array(ia[:]), np.array(ib[:]), nau.value, nbu.value)
+
+
+def dso_set_wait_probe(ctx, polls):
+    """Diagnostics: a bounded wait in the TMA variant that must give up."""
+    _check(load().dso_set_wait_probe(ctx, int(polls)), "dso_set_wait_probe")
+
+
+def dso_psi_device_pointer(ctx) -> int:
+    """Device address of the context's psi (borrowed; see include/dso.h)."""
+    p = ctypes.c_void_p()
+    _check(load().dso_psi_device_pointer(ctx, ctypes.byref(p)), "dso_psi_device_pointer")
+    return int(p.value)
+
+
+def device_view(ptr: int, shape, dtype, device=0):
+    """A torch tensor that views `shape` elements of `dtype` at device address
+    `ptr` without a copy (through __cuda_array_interface__); the memory stays
+    owned by whoever allocated it."""
+    import torch
+    typestr = {np.dtype(np.complex128): "<c16", np.dtype(np.complex64): "<c8",
+               np.dtype(np.float64): "<f8"}[np.dtype(dtype)]
+
+    class _View:
+        __cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                    "data": (int(ptr), False), "version": 3, "strides": None}
+    return torch.as_tensor(_View(), device=f"cuda:{device}")
 
 
 def dso_tuned_plan(ctx) -> str:
@@ -368,6 +419,14 @@ class Context:
 
     def observables(self):
         return dso_observables(self.ctx, self.S, self.B)
+
+    def inner(self, phi):
+        """<psi|phi> per job (Sec. II A); omega = -2 Im of it."""
+        return dso_inner(self.ctx, np.ascontiguousarray(phi, dtype=self.dtype) if isinstance(phi, np.ndarray)
+                         else phi, self.B)
+
+    def phase_at_density_maximum(self):
+        return dso_phase_at_density_maximum(self.ctx, self.S, self.B)
 
     def close(self):
         if self.ctx is not None:

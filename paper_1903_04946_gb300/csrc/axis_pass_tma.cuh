@@ -41,10 +41,14 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-// Bounded wait on phase `parity`: false if it did not complete in time.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Bounded wait on phase `parity`: false if it did not complete within
+// `limit` polls.  The waits for tile copies use kWaitPolls; the drain of
+// copies still in flight after an error always uses kWaitPolls too, so that
+// no CTA leaves while a copy into its shared memory can still land.
+constexpr int kWaitPolls = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit = kWaitPolls) {
   const unsigned a = smem_u32(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -190,7 +194,7 @@ __host__ __device__ constexpr int tma_np_tab() {
 }
 
 // Dynamic shared memory needed by axis_pass_tma_kernel (128 bytes of slack
-// for aligning the base, 64 for the barriers and the status word).
+// for aligning the base, 64 for the four barriers and the status word).
 template <int L, int SV>
 inline size_t tma_smem_bytes(int G) {
   return (size_t)(SV + tma_np_tab<L, SV>()) * G * L * 16 + (size_t)L * 16 + 128 + 64;
@@ -219,8 +223,8 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
   double2* x = sm;
   double2* tb = sm + (size_t)SV * tile_pts;
   double2* tws = tb + (size_t)np_tab * tile_pts;
-  unsigned long long* bar = (unsigned long long*)(tws + L);
-  volatile int* status = (volatile int*)(bar + 3);
+  unsigned long long* bar = (unsigned long long*)(tws + L);  // [0..2] copies, [3] wait diagnostics
+  volatile int* status = (volatile int*)(bar + 4);
 
   // tile geometry (the same as axis_pass_kernel)
   const TileJob tj = split_tile(blockIdx.x, SV, a);
@@ -255,12 +259,33 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
       tma_load_5d(tb, &maps.tab, 0, c1, 0, c3, a.ub, &bar[1]);
     }
   }
-  if (!cta_wait(&bar[0], 0, status, tid)) {
+  // copies in flight, tracked by thread 0: bit b for bar[b]
+  unsigned pending = (tid == 0) ? (1u | ((vstep || tstep) ? 2u : 0u)) : 0u;
+  // a wait gave up: record it and let every copy this CTA started land
+  // before the CTA leaves (each drain wait again bounded)
+  auto give_up = [&](int code) {
     if (tid == 0) {
-      atomicExch(a.err, 1);
-      mbar_wait(&bar[1], 0);  // bounded: let the table copy in flight land
+      atomicExch(a.err, code);
+      if (pending & 1u) mbar_wait(&bar[0], 0);
+      if (pending & 2u) mbar_wait(&bar[1], 0);
+      if (pending & 4u) mbar_wait(&bar[2], 0);
     }
+  };
+  if (!cta_wait(&bar[0], 0, status, tid)) {
+    give_up(1);
     return;
+  }
+  pending &= ~1u;
+  if (a.wait_probe > 0) {
+    // diagnostics of the bounded waits: a barrier that no copy completes;
+    // the wait must give up after a.wait_probe polls and record a timeout
+    // (code 5).  No copy is involved, and the tile's work goes on unchanged.
+    if (tid == 0) {
+      mbar_init(&bar[3], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      if (!mbar_wait(&bar[3], 0, a.wait_probe)) atomicExch(a.err, 5);
+    }
+    __syncthreads();
   }
   pdl_trigger();
 
@@ -270,9 +295,10 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
   }
   if (vstep) {
     if (!cta_wait(&bar[1], 0, status, tid)) {
-      if (tid == 0) atomicExch(a.err, 2);
+      give_up(2);
       return;
     }
+    pending &= ~2u;
     tma_potential<SV>(x, tb, tile_pts, tid, nthr, a.dec0);
     __syncthreads();
     if (a.U2) {
@@ -284,15 +310,17 @@ __global__ void __launch_bounds__(256) axis_pass_tma_kernel(PassArgs a, const __
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(&bar[2], (unsigned)(tile_pts * sizeof(double2)));
       tma_load_5d(tb, &maps.tab2, 0, c1, 0, c3, a.ub, &bar[2]);
+      pending |= 4u;
     }
   }
   if (a.flags & PASS_FWD) tma_fft<L, false>(x, tws, G, Wi_log2, nslots, tid, nthr);
   if (tstep) {
     __syncthreads();
     if (!cta_wait(&bar[vstep ? 2 : 1], 0, status, tid)) {
-      if (tid == 0) atomicExch(a.err, 3);
+      give_up(3);
       return;
     }
+    pending = 0u;
     for (int e = tid; e < tile_pts; e += nthr) {
       const double2 ph = tb[e];
 #pragma unroll

@@ -146,6 +146,7 @@ struct dso_ctx {
   double norm_tol = 0.0;
   std::vector<double> norm_ref;
   double* norm_part = nullptr;
+  size_t norm_part_cap = 0;  // doubles in norm_part
   // graph of one middle time step
   cudaGraphExec_t step_exec = nullptr;
   int step_exec_passes = 0;
@@ -154,6 +155,7 @@ struct dso_ctx {
   int variant[DSO_MAX_VAXES][2] = {};
   int cps[DSO_MAX_VAXES][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
   int pdl = 0;               // programmatic dependent launch between passes (DSO_PDL=1: on)
+  int wait_probe = 0;        // dso_set_wait_probe: polls of the TMA variant's diagnostic wait (0: off)
   unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
   int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
@@ -195,6 +197,7 @@ void drop_model(dso_ctx* c) {
   dfree(c->partials);
   dfree(c->obs_out);
   dfree(c->norm_part);
+  c->norm_part_cap = 0;
   for (auto& x : c->xtw) dfree(x);
   c->norm_ref.clear();
   c->have_V = c->have_psi = false;
@@ -331,6 +334,7 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.dec0 = c->dec0;
   a.ctas_per_sm = c->cps[p.axis][which];
   a.pdl = c->pdl;
+  a.wait_probe = c->wait_probe;
   const long long ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G)
                                           : (long long)c->B * c->S * (a.lines / a.G);
   const int variant = c->variant[p.axis][which];
@@ -961,7 +965,11 @@ __global__ void norm_partial_kernel(const void* __restrict__ psi, long long per_
 
 // Squared norms of every job's psi (synchronises the stream).
 static dso_status job_norms(dso_ctx* c, std::vector<double>& out) {
-  if (!c->norm_part) CK(cudaMalloc(&c->norm_part, (size_t)c->B * kNormBlocks * sizeof(double)));
+  if (!c->norm_part || c->norm_part_cap < (size_t)c->B * kNormBlocks) {
+    dfree(c->norm_part);
+    CK(cudaMalloc(&c->norm_part, (size_t)c->B * kNormBlocks * sizeof(double)));
+    c->norm_part_cap = (size_t)c->B * kNormBlocks;
+  }
   norm_partial_kernel<<<dim3(kNormBlocks, c->B), 256, 0, c->stream>>>(c->psi, (long long)c->S * c->P,
                                                                        c->prec == DSO_FP32 ? 1 : 0, c->norm_part);
   CK(cudaGetLastError());
@@ -973,6 +981,100 @@ static dso_status job_norms(dso_ctx* c, std::vector<double>& out) {
   for (int b = 0; b < c->B; ++b)
     for (int k = 0; k < kNormBlocks; ++k) out[b] += h[(size_t)b * kNormBlocks + k];
   return DSO_OK;
+}
+
+// Per-job inner products sum conj(psi) phi (no grid measure): block k of job
+// b writes the real and imaginary parts of its grid-stride share to
+// part[(b * kNormBlocks + k) * 2 + {0, 1}]; the host adds them in order.
+__global__ void inner_partial_kernel(const void* __restrict__ psi, const void* __restrict__ phi, long long per_job,
+                                     int fp32, double* part) {
+  __shared__ double red_re[256], red_im[256];
+  const int b = blockIdx.y;
+  double ar = 0.0, ai = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_job;
+       i += (long long)gridDim.x * blockDim.x) {
+    double xr, xi, yr, yi;
+    if (fp32) {
+      const float2 x = static_cast<const float2*>(psi)[b * per_job + i];
+      const float2 y = static_cast<const float2*>(phi)[b * per_job + i];
+      xr = x.x, xi = x.y, yr = y.x, yi = y.y;
+    } else {
+      const double2 x = static_cast<const double2*>(psi)[b * per_job + i];
+      const double2 y = static_cast<const double2*>(phi)[b * per_job + i];
+      xr = x.x, xi = x.y, yr = y.x, yi = y.y;
+    }
+    ar = fma(xr, yr, fma(xi, yi, ar));   // Re conj(x) y = xr yr + xi yi
+    ai = fma(xr, yi, fma(-xi, yr, ai));  // Im conj(x) y = xr yi - xi yr
+  }
+  red_re[threadIdx.x] = ar;
+  red_im[threadIdx.x] = ai;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red_re[threadIdx.x] += red_re[threadIdx.x + w];
+      red_im[threadIdx.x] += red_im[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[(b * kNormBlocks + blockIdx.x) * 2] = red_re[0];
+    part[(b * kNormBlocks + blockIdx.x) * 2 + 1] = red_im[0];
+  }
+}
+
+// Largest density |psi_s(q)|^2 of every (job, surface) row: block k of row r
+// writes its (density, first index of it, re, im) to part[(r * kNormBlocks + k)
+// * 4 + {0..3}] (the index as a double: exact below 2^53).  Ties keep the
+// smallest index, so the host's in-order reduction gives the first maximum in
+// storage order.
+__global__ void density_max_kernel(const void* __restrict__ psi, long long P, int fp32, double* part) {
+  __shared__ double rd[256], ri[256];
+  __shared__ long long rx[256];
+  const long long row = blockIdx.y;
+  double best = -1.0, br = 0.0, bi = 0.0;
+  long long bx = -1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+    double re, im;
+    if (fp32) {
+      const float2 v = static_cast<const float2*>(psi)[row * P + i];
+      re = v.x, im = v.y;
+    } else {
+      const double2 v = static_cast<const double2*>(psi)[row * P + i];
+      re = v.x, im = v.y;
+    }
+    const double d = re * re + im * im;
+    if (d > best) {  // i grows: a later equal value never replaces
+      best = d, bx = i, br = re, bi = im;
+    }
+  }
+  rd[threadIdx.x] = best;
+  rx[threadIdx.x] = bx;
+  ri[threadIdx.x] = br;
+  __syncthreads();
+  __shared__ double rim[256];
+  rim[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const int o = threadIdx.x + w;
+      const bool take = rd[o] > rd[threadIdx.x] ||
+                        (rd[o] == rd[threadIdx.x] && rx[o] >= 0 && (rx[threadIdx.x] < 0 || rx[o] < rx[threadIdx.x]));
+      if (take) {
+        rd[threadIdx.x] = rd[o];
+        rx[threadIdx.x] = rx[o];
+        ri[threadIdx.x] = ri[o];
+        rim[threadIdx.x] = rim[o];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* out = part + (row * kNormBlocks + blockIdx.x) * 4;
+    out[0] = rd[0];
+    out[1] = (double)rx[0];
+    out[2] = ri[0];
+    out[3] = rim[0];
+  }
 }
 
 // A user composition: 1..4096 finite nonzero elementary coefficients,
@@ -1032,6 +1134,21 @@ dso_status dso_set_composition(dso_ctx* c, int m, const double* gamma, int eleme
   } catch (const std::exception& ex) {
     return fail(DSO_EINVAL, ex.what());
   }
+  return DSO_OK;
+}
+
+dso_status dso_set_wait_probe(dso_ctx* c, int polls) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (polls < 0) return fail(DSO_EINVAL, "polls must be >= 0");
+  c->wait_probe = polls;
+  drop_graph(c);  // the captured step carries the launch arguments
+  return DSO_OK;
+}
+
+dso_status dso_psi_device_pointer(dso_ctx* c, void** out) {
+  if (!c || !out) return fail(DSO_EINVAL, "null argument");
+  if (!c->psi) return fail(DSO_ESTATE, "load the potential first (it allocates psi)");
+  *out = c->psi;
   return DSO_OK;
 }
 
@@ -1166,6 +1283,8 @@ static dso_status check_device_flag(dso_ctx* c) {
       for (int i = 2; i < 10; ++i) ctx_info += " " + std::to_string(h[i]);
     if (h[0] >= 100)
       return fail(DSO_ECUDA, "bounds check failed in an axis pass (code " + std::to_string(h[0]) + ")" + ctx_info);
+    if (h[0] == 5)
+      return fail(DSO_ETIMEOUT, "the diagnostic bounded wait (dso_set_wait_probe) gave up, as it must (code 5)");
     return fail(DSO_ETIMEOUT, "a kernel's bounded wait for its tile copy gave up (code " + std::to_string(h[0]) + ")");
   }
   return DSO_OK;
@@ -1247,6 +1366,81 @@ dso_status dso_observables(dso_ctx* c, double* norm, double* energy, double* pop
     finite = finite && std::isfinite(tot) && std::isfinite(hb[c->S]) && std::isfinite(hb[c->S + 1]);
   }
   if (!finite) return fail(DSO_ENUMERIC, "non-finite observable");
+  return DSO_OK;
+}
+
+dso_status dso_inner(dso_ctx* c, const void* phi, int where, double* re, double* im) {
+  NvtxRange nvtx("dso_inner");
+  if (!c || !phi) return fail(DSO_EINVAL, "null argument");
+  if (!c->have_psi) return fail(DSO_ESTATE, "wavefunction not set");
+  if (where != DSO_HOST && where != DSO_DEVICE) return fail(DSO_EINVAL, "where must be DSO_HOST or DSO_DEVICE");
+  DeviceGuard g(c->device);
+  const size_t bytes = (size_t)c->B * c->S * c->P * c->esz();
+  const void* dphi = phi;
+  if (where == DSO_HOST) {  // staged in the work buffer
+    if (!c->work) CK(cudaMalloc(&c->work, bytes));
+    CK(cudaMemcpyAsync(c->work, phi, bytes, cudaMemcpyHostToDevice, c->stream));
+    dphi = c->work;
+  }
+  if (!c->norm_part || c->norm_part_cap < (size_t)c->B * kNormBlocks * 4) {
+    dfree(c->norm_part);
+    CK(cudaMalloc(&c->norm_part, (size_t)c->B * kNormBlocks * 4 * sizeof(double)));
+    c->norm_part_cap = (size_t)c->B * kNormBlocks * 4;
+  }
+  inner_partial_kernel<<<dim3(kNormBlocks, c->B), 256, 0, c->stream>>>(c->psi, dphi, (long long)c->S * c->P,
+                                                                        c->prec == DSO_FP32 ? 1 : 0, c->norm_part);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  std::vector<double> h((size_t)c->B * kNormBlocks * 2);
+  CK(cudaMemcpyAsync(h.data(), c->norm_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double dV = 1.0;
+  for (int d = 0; d < c->D; ++d) dV *= (c->qmax[d] - c->qmin[d]) / (double)c->n[d];
+  for (int b = 0; b < c->B; ++b) {
+    double sr = 0.0, si = 0.0;
+    for (int k = 0; k < kNormBlocks; ++k) {
+      sr += h[((size_t)b * kNormBlocks + k) * 2];
+      si += h[((size_t)b * kNormBlocks + k) * 2 + 1];
+    }
+    if (re) re[b] = sr * dV;
+    if (im) im[b] = si * dV;
+  }
+  return DSO_OK;
+}
+
+dso_status dso_phase_at_density_maximum(dso_ctx* c, int64_t* index, double* phase) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (!c->have_psi) return fail(DSO_ESTATE, "wavefunction not set");
+  DeviceGuard g(c->device);
+  const long long rows = (long long)c->B * c->S;
+  if (rows > 65535) return fail(DSO_EINVAL, "at most 65535 job surfaces");
+  if (!c->norm_part || c->norm_part_cap < (size_t)rows * kNormBlocks * 4) {
+    dfree(c->norm_part);
+    CK(cudaMalloc(&c->norm_part, (size_t)rows * kNormBlocks * 4 * sizeof(double)));
+    c->norm_part_cap = (size_t)rows * kNormBlocks * 4;
+  }
+  density_max_kernel<<<dim3(kNormBlocks, (unsigned)rows), 256, 0, c->stream>>>(c->psi, c->P,
+                                                                             c->prec == DSO_FP32 ? 1 : 0,
+                                                                             c->norm_part);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  std::vector<double> h((size_t)rows * kNormBlocks * 4);
+  CK(cudaMemcpyAsync(h.data(), c->norm_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (long long r = 0; r < rows; ++r) {
+    double best = -1.0, br = 0.0, bi = 0.0;
+    long long bx = -1;
+    for (int k = 0; k < kNormBlocks; ++k) {
+      const double* p = &h[((size_t)r * kNormBlocks + k) * 4];
+      const long long x = (long long)p[1];
+      if (x < 0) continue;
+      if (p[0] > best || (p[0] == best && x < bx)) {
+        best = p[0], bx = x, br = p[2], bi = p[3];
+      }
+    }
+    if (index) index[r] = bx;
+    if (phase) phase[r] = std::atan2(bi, br);
+  }
   return DSO_OK;
 }
 

@@ -47,6 +47,7 @@ struct PassArgs {
   const void* xtw;         // PASS_XTW: split-axis twiddles [n1][n2], w_n^(k1 i2), or null
   int xtw_n2_log2;         // log2 n2 (length of the second factor of the split axis)
   int xtw_s2_log2;         // log2 of the second factor's stride (product of the later axes)
+  int wait_probe;          // > 0: TMA variant's bounded-wait diagnostics (polls of a barrier no copy completes)
 };
 
 // Tile index -> (first staged surface over all jobs, job).  A pass staging

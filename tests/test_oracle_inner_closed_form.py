@@ -123,3 +123,34 @@ def test_inner_orthogonal_surfaces_vanish():
     phi = _state(pr, [0.0, 1.0], [[(0.0, 0.0, 1.0)], [(0.0, 0.0, 1.0)]])
     assert O.inner(pr, psi, phi) == 0.0
     assert O.symplectic_form(pr, psi, phi) == 0.0
+
+
+def test_phase_at_density_maximum_closed_forms():
+    # a Gaussian of known global phase: the density peaks at its centre
+    pr = _problem((256,), (-10.0,), (10.0,), 2)
+    q = synth.axis_points(256, -10.0, 10.0)
+    dq = 20.0 / 256
+    q0 = q[137]  # centre on a grid point
+    psi = np.zeros((2, 256), complex)
+    psi[0] = np.exp(1j * 0.7) * gauss_1d(q, q0, 0.0, 0.9)
+    psi[1] = np.exp(-1j * 2.9) * 0.3 * gauss_1d(q, q[40], 1.3, 0.5)  # momentum: phase 0 at the centre
+    idx, ph = O.phase_at_density_maximum(pr, psi)
+    assert list(idx) == [137, 40]
+    assert ph[0] == pytest.approx(0.7, abs=1e-15)
+    assert ph[1] == pytest.approx(-2.9, abs=1e-15)
+    # a coherent state of a harmonic oscillator (m = 1, omega = 1, sigma = 1,
+    # p0 = 0) after time t: psi = pi^-1/4 exp(-(q - q0 cos t)^2 / 2
+    # - i (q q0 sin t - q0^2 sin 2t / 4) - i t / 2); at the density maximum
+    # q = q0 cos t the phase is -(q0^2 sin 2t)/4 - t/2 (mod 2 pi)
+    t, q0c = 0.8, 1.5
+    qc = q0c * np.cos(t)
+    kk = int(np.argmin(np.abs(q - qc)))
+    qg = q - (q[kk] - qc)  # shift the grid so that qc is a grid point
+    coh = np.pi ** -0.25 * np.exp(-(qg - qc) ** 2 / 2 - 1j * (qg * q0c * np.sin(t) - q0c ** 2 * np.sin(2 * t) / 4)
+                                  - 1j * t / 2)
+    psi2 = np.stack([coh, np.zeros_like(coh)])
+    idx2, ph2 = O.phase_at_density_maximum(pr, psi2)
+    want = np.angle(np.exp(1j * (-(q0c ** 2) * np.sin(2 * t) / 4 - t / 2)))
+    assert idx2[0] == kk
+    assert ph2[0] == pytest.approx(want, abs=1e-14)
+    assert dq > 0
