@@ -322,6 +322,72 @@ dso_status dso_position_observables_noalloc(const void* psi, const double* V, in
  * denominator of the instruction-rate roofline of the FP64 kernels. */
 dso_status dso_fp64_issue_rate(int device, double* inst_per_s);
 
+/* Pass limits of a context: an axis longer than max_line points, or an axis
+ * 0 whose S surfaces exceed max_tile points, is transformed as two virtual
+ * axes (four-step FFT, see dso_set_grid).  Powers of two, max_line in
+ * [8, 4096] (default 4096), max_tile in [16, 8192] (default 8192).  Smaller
+ * limits give smaller tiles (more of them, for small grids) at the cost of
+ * more passes; a grid that no longer fits (a split factor above max_line)
+ * returns DSO_EINVAL and keeps the old limits.  Takes effect at once when the
+ * potential is loaded (the state is kept), else at dso_load_potential.  A
+ * context added to a batch gets the batch's limits (1024, 2048); setting the
+ * same limits on a context that propagates alone gives it the batch's pass
+ * layout, so that the two give bitwise the same result.  The paper has no
+ * counterpart. */
+dso_status dso_set_pass_limits(dso_ctx* ctx, int max_line, int max_tile);
+
+/* Batch slots (continuous batching).  A batch advances many jobs -- each a
+ * context with its own grid, surfaces, masses, potential, scheme and state,
+ * all of the batch's precision and device -- by one composed time step of
+ * each job per launch of one persistent kernel: the launch's work list holds
+ * every pass of every unfinished job (tiles of one pass of one job wait for
+ * the job's previous pass through a counter; the waits are bounded).  Jobs
+ * with uneven grids and different schemes, time steps and step counts share
+ * the launch; jobs join (dso_batch_add) and leave (dso_batch_retire) between
+ * steps.  Each job's result is bitwise the same as the job propagated alone
+ * with the batch's pass limits (dso_set_pass_limits(ctx, 1024, 2048)), and
+ * so within round-off of the job alone with the defaults.
+ *
+ * dso_batch_create: an empty batch on `device`, with precision DSO_FP64 or
+ * DSO_FP32, working on `cuda_stream` (NULL: a stream the batch owns).
+ * dso_batch_destroy: releases the batch; the jobs' contexts stay the
+ * caller's. */
+typedef struct dso_batch dso_batch;
+dso_status dso_batch_create(dso_batch** out, int device, int precision, void* cuda_stream);
+void dso_batch_destroy(dso_batch* batch);
+
+/* Add a ready context (grid, masses, potential, scheme and psi set) as a job
+ * that is to advance its psi by time t with step dt (t/dt a non-negative
+ * integer within 1e-9 relative, dt may be negative), as dso_propagate(ctx, t,
+ * dt) would.  The context is borrowed until dso_batch_retire: the caller must
+ * not use it meanwhile.  Its tables are built for dt and its passes re-planned
+ * with the batch's limits; *slot receives the job's slot.  DSO_EINVAL for a
+ * grid too large for a slot (lines above 1024 points after one split, or
+ * S x n1 above 2048 on axis 0): such a job fills the GPU alone. */
+dso_status dso_batch_add(dso_batch* batch, dso_ctx* job, double t, double dt, int* slot);
+
+/* Enqueue one composed step of every unfinished job (its first step's passes
+ * the first time, the final pass after its last step): one launch of the
+ * work-list kernel, asynchronous on the batch's stream.  *active (may be
+ * NULL) receives the number of jobs still unfinished after this step.  Waits
+ * for the previous launch before reusing its host-side list. */
+dso_status dso_batch_step(dso_batch* batch, int* active);
+
+/* Wait for the batch's work and report a bounded wait that gave up
+ * (DSO_ETIMEOUT). */
+dso_status dso_batch_sync(dso_batch* batch);
+
+/* Steps done and steps in all of the job in `slot`. */
+dso_status dso_batch_slot_status(const dso_batch* batch, int slot, int64_t* steps_done, int64_t* steps_total);
+
+/* Remove the job in `slot` (finished or not) and hand its context back to
+ * the caller, whose psi then holds the job's state (synchronises the batch's
+ * stream).  The slot is free for a later dso_batch_add. */
+dso_status dso_batch_retire(dso_batch* batch, int slot);
+
+/* Launches of the work-list kernel this batch has issued. */
+int64_t dso_batch_launch_count(const dso_batch* batch);
+
 /* Message for the last failed call on this thread (never NULL; valid until
  * the next call on this thread). */
 const char* dso_last_error(void);

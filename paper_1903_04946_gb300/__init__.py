@@ -28,7 +28,9 @@ EXPORTS = (
     "dso_scheme_coefficients", "dso_profile_steps", "dso_launch_count", "dso_last_error",
     "dso_position_observables_noalloc", "dso_busy", "dso_tuned_plan", "dso_set_composition",
     "dso_composition_coefficients", "dso_set_norm_check", "dso_fp64_issue_rate", "dso_inner",
-    "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer",
+    "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer", "dso_set_pass_limits",
+    "dso_batch_create", "dso_batch_destroy", "dso_batch_add", "dso_batch_step", "dso_batch_sync",
+    "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count",
 )
 
 _lib = None
@@ -78,6 +80,15 @@ def load(path: str = LIB):
         "dso_phase_at_density_maximum": (i32, [vp, ctypes.POINTER(i64), pd]),
         "dso_set_wait_probe": (i32, [vp, i32]),
         "dso_psi_device_pointer": (i32, [vp, ctypes.POINTER(vp)]),
+        "dso_set_pass_limits": (i32, [vp, i32, i32]),
+        "dso_batch_create": (i32, [ctypes.POINTER(vp), i32, i32, vp]),
+        "dso_batch_destroy": (None, [vp]),
+        "dso_batch_add": (i32, [vp, vp, dbl, dbl, ctypes.POINTER(i32)]),
+        "dso_batch_step": (i32, [vp, ctypes.POINTER(i32)]),
+        "dso_batch_sync": (i32, [vp]),
+        "dso_batch_slot_status": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "dso_batch_retire": (i32, [vp, i32]),
+        "dso_batch_launch_count": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -299,6 +310,92 @@ def device_view(ptr: int, shape, dtype, device=0):
         __cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
                                     "data": (int(ptr), False), "version": 3, "strides": None}
     return torch.as_tensor(_View(), device=f"cuda:{device}")
+
+
+def dso_set_pass_limits(ctx, max_line, max_tile):
+    _check(load().dso_set_pass_limits(ctx, int(max_line), int(max_tile)), "dso_set_pass_limits")
+
+
+def dso_batch_create(device: int = 0, precision: int = DSO_FP64, stream=None):
+    b = ctypes.c_void_p()
+    _check(load().dso_batch_create(ctypes.byref(b), device, precision, _stream_handle(stream)), "dso_batch_create")
+    return b
+
+
+def dso_batch_destroy(batch):
+    load().dso_batch_destroy(batch)
+
+
+def dso_batch_add(batch, ctx, t, dt) -> int:
+    slot = ctypes.c_int()
+    _check(load().dso_batch_add(batch, ctx, float(t), float(dt), ctypes.byref(slot)), "dso_batch_add")
+    return slot.value
+
+
+def dso_batch_step(batch) -> int:
+    active = ctypes.c_int()
+    _check(load().dso_batch_step(batch, ctypes.byref(active)), "dso_batch_step")
+    return active.value
+
+
+def dso_batch_sync(batch):
+    _check(load().dso_batch_sync(batch), "dso_batch_sync")
+
+
+def dso_batch_slot_status(batch, slot):
+    done, total = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().dso_batch_slot_status(batch, int(slot), ctypes.byref(done), ctypes.byref(total)),
+           "dso_batch_slot_status")
+    return done.value, total.value
+
+
+def dso_batch_retire(batch, slot):
+    _check(load().dso_batch_retire(batch, int(slot)), "dso_batch_retire")
+
+
+def dso_batch_launch_count(batch) -> int:
+    return int(load().dso_batch_launch_count(batch))
+
+
+class Batch:
+    """Batch slots: Context objects join with their own t and dt, advance
+    one composed step per launch, and leave when retired."""
+
+    def __init__(self, device: int = 0, precision: int = DSO_FP64, stream=None):
+        self.b = dso_batch_create(device, precision, stream)
+        self.jobs = {}
+
+    def add(self, ctx: "Context", t, dt) -> int:
+        slot = dso_batch_add(self.b, ctx.ctx, t, dt)
+        self.jobs[slot] = ctx
+        return slot
+
+    def step(self) -> int:
+        return dso_batch_step(self.b)
+
+    def run(self):
+        """Step until every job has finished."""
+        while self.step() > 0:
+            pass
+        dso_batch_sync(self.b)
+
+    def status(self, slot):
+        return dso_batch_slot_status(self.b, slot)
+
+    def retire(self, slot) -> "Context":
+        dso_batch_retire(self.b, slot)
+        return self.jobs.pop(slot)
+
+    def close(self):
+        if self.b is not None:
+            dso_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dso_tuned_plan(ctx) -> str:

@@ -156,6 +156,8 @@ struct dso_ctx {
   int cps[DSO_MAX_VAXES][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
   int pdl = 0;               // programmatic dependent launch between passes (DSO_PDL=1: on)
   int wait_probe = 0;        // dso_set_wait_probe: polls of the TMA variant's diagnostic wait (0: off)
+  int max_line = DSO_MAX_LINE;  // dso_set_pass_limits: longest pass line,
+  int max_tile = 8192;          // and most points of the S surfaces of an axis-0 line
   unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
   int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
@@ -204,25 +206,33 @@ void drop_model(dso_ctx* c) {
 }
 
 // Virtual axes of the passes for the grid and S surfaces (VLayout): a grid
-// axis longer than a pass line (DSO_MAX_LINE), or an axis 0 whose S surfaces
-// do not fit the potential pass's tile (S n > 8192), is split into
-// n1 = 2^floor(log2(n) / 2) and n2 = n / n1 (both <= 2048 for n <= 2^22, so
-// S n1 <= 8192 for every S <= 4).
-void plan_virtual(dso_ctx* c) {
+// axis longer than a pass line (max_line), or an axis 0 whose S surfaces do
+// not fit the potential pass's tile (S n > max_tile), is split into
+// n1 = 2^floor(log2(n) / 2) (halved further on axis 0 until S n1 <= max_tile)
+// and n2 = n / n1.  With the default limits (4096, 8192) every axis up to 2^22
+// points splits into factors <= 2048 and S n1 <= 8192 for every S <= 4; with
+// tighter limits a grid may not fit, and the plan fails (false).
+bool plan_virtual(dso_ctx* c) {
   c->Dv = 0;
   for (int d = 0; d < c->D; ++d) {
     const int64_t n = c->n[d];
-    if (n > DSO_MAX_LINE || (d == 0 && (long long)c->S * n > 8192)) {
-      const int64_t n1 = 1LL << (ilog2(n) / 2);
+    if (n > c->max_line || (d == 0 && (long long)c->S * n > c->max_tile)) {
+      int64_t n1 = 1LL << (ilog2(n) / 2);
+      while (d == 0 && (long long)c->S * n1 > c->max_tile && n1 > 8) n1 /= 2;
+      const int64_t n2 = n / n1;
+      if (n1 < 8 || n2 < 8 || n1 > c->max_line || n2 > c->max_line ||
+          (d == 0 && (long long)c->S * n1 > c->max_tile))
+        return false;
       c->nv[c->Dv] = n1;
       c->vpart[c->Dv++] = 1;
-      c->nv[c->Dv] = n / n1;
+      c->nv[c->Dv] = n2;
       c->vpart[c->Dv++] = 2;
     } else {
       c->nv[c->Dv] = n;
       c->vpart[c->Dv++] = 0;
     }
   }
+  return true;
 }
 
 VLayout vlayout(const dso_ctx* c) {
@@ -252,6 +262,27 @@ int choose_G(const dso_ctx* c, int L, int SV) {
   long long G = 1;
   while (G * 2 <= target && G * 2 <= gmax && G * 2 <= lines) G *= 2;
   return (int)G;
+}
+
+// (Re)plan the virtual axes of a context whose S is known, and reset the
+// per-kind tile line counts and kernel variants (the tables, graph and
+// tuning that depend on the layout are dropped).
+dso_status replan(dso_ctx* c) {
+  if (!plan_virtual(c)) return fail(DSO_EINVAL, "the grid does not fit the pass limits (a split factor exceeds them)");
+  for (int d = 0; d < c->Dv; ++d) {
+    // every pass line fits one tile: S surfaces of a virtual axis-0 line,
+    // one surface of any other
+    if (!axis_pass_supported((int)c->nv[d], d == 0 ? c->S : 1))
+      return fail(DSO_EINVAL, "internal: a pass line does not fit a tile");
+    c->G[d][0] = choose_G(c, (int)c->nv[d], 1);
+    c->G[d][1] = choose_G(c, (int)c->nv[d], c->S);
+    c->variant[d][0] = c->variant[d][1] = 0;
+    c->cps[d][0] = c->cps[d][1] = 0;
+  }
+  for (auto& x : c->xtw) dfree(x);
+  drop_tables(c);
+  c->tuned = false;
+  return DSO_OK;
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once (no -lcuda).
@@ -286,9 +317,11 @@ bool encode_view(CUtensorMap* m, const void* base, long long P, int L, long long
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t run_pass(dso_ctx* c, const Pass& p) {
+// The kernel arguments of pass p (and the number of its tiles), with the
+// tile line count the context holds for the pass's kind.
+cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& ntiles) {
   const int L = (int)c->nv[p.axis];
-  PassArgs a{};  // every field defined; the kernels read all of them
+  a = PassArgs{};  // every field defined; the kernels read all of them
   const size_t es = c->esz();
   a.psi = c->psi;
   const int NP = c->S * (c->S + 1) / 2;
@@ -335,8 +368,20 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   a.ctas_per_sm = c->cps[p.axis][which];
   a.pdl = c->pdl;
   a.wait_probe = c->wait_probe;
-  const long long ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G)
-                                          : (long long)c->B * c->S * (a.lines / a.G);
+  ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G) : (long long)c->B * c->S * (a.lines / a.G);
+  return cudaSuccess;
+}
+
+cudaError_t run_pass(dso_ctx* c, const Pass& p) {
+  const int L = (int)c->nv[p.axis];
+  PassArgs a;
+  long long ntiles = 0;
+  {
+    const cudaError_t e = build_pass_args(c, p, a, ntiles);
+    if (e != cudaSuccess) return e;
+  }
+  const long long stride = a.stride;
+  const int which = p.SV == 1 ? 0 : 1;
   const int variant = c->variant[p.axis][which];
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
@@ -883,17 +928,12 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
     CK(cudaMemsetAsync(c->err, 0, 16 * sizeof(int), c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
-  plan_virtual(c);
-  for (int d = 0; d < c->Dv; ++d) {
-    // every pass line fits one tile: S surfaces of a virtual axis-0 line,
-    // one surface of any other
-    if (!axis_pass_supported((int)c->nv[d], d == 0 ? S : 1)) {
+  {
+    const dso_status pst = replan(c);
+    if (pst != DSO_OK) {
       drop_model(c);
-      return fail(DSO_EINVAL, "internal: a pass line does not fit a tile");
+      return pst;
     }
-    c->G[d][0] = choose_G(c, (int)c->nv[d], 1);
-    c->G[d][1] = choose_G(c, (int)c->nv[d], S);
-    c->variant[d][0] = c->variant[d][1] = 0;
   }
   c->have_V = true;
   return DSO_OK;
@@ -1560,6 +1600,333 @@ int dso_tuned_plan(const dso_ctx* c, char* out, int cap) {
   std::memcpy(out, s.c_str(), s.size() + 1);
   return (int)s.size();
 }
+
+dso_status dso_set_pass_limits(dso_ctx* c, int max_line, int max_tile) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (max_line < 8 || max_line > DSO_MAX_LINE || (max_line & (max_line - 1)) || max_tile < 16 || max_tile > 8192 ||
+      (max_tile & (max_tile - 1)))
+    return fail(DSO_EINVAL, "max_line must be a power of two in [8, 4096] and max_tile one in [16, 8192]");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  const int ol = c->max_line, ot = c->max_tile;
+  c->max_line = max_line;
+  c->max_tile = max_tile;
+  if (c->have_V) {  // S is known: plan again (psi is in the position representation: unaffected)
+    const dso_status st = replan(c);
+    if (st != DSO_OK) {
+      c->max_line = ol;
+      c->max_tile = ot;
+      const dso_status back = replan(c);
+      (void)back;
+      return st;
+    }
+  }
+  return DSO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch slots: many jobs (contexts) with uneven grids advance by one composed
+// step per persistent launch of the work-list kernel (batch.cu).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kBatchMaxLine = 1024;  // batch tiles hold at most 2048 amplitudes:
+constexpr int kBatchMaxTile = 2048;  // lines of <= 1024 points, S n1 <= 2048 on axis 0
+
+struct BatchSlot {
+  dso_ctx* ctx = nullptr;
+  double dt = 0.0;
+  long long steps_total = 0, steps_done = 0;
+  bool live = false;
+  std::vector<BatchPass> first, mid, fin;  // pass lists of a first, a middle and the final step
+};
+
+}  // namespace
+
+struct dso_batch {
+  int device = 0;
+  int prec = DSO_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<BatchSlot> slots;
+  // device work list of the next launch
+  BatchPass* d_pass = nullptr;
+  size_t pass_cap = 0;
+  BatchSeg* d_seg = nullptr;
+  size_t seg_cap = 0;
+  unsigned* d_done = nullptr;  // per-segment completion counters
+  size_t done_cap = 0;
+  unsigned long long* d_head = nullptr;
+  int* d_err = nullptr;
+  std::vector<BatchPass> h_pass;  // host copies of the last launch's list (kept until it completes)
+  std::vector<BatchSeg> h_seg;
+  int64_t launches = 0;
+};
+
+namespace {
+
+dso_status batch_reserve(dso_batch* b, size_t npass, size_t nseg) {
+  if (npass > b->pass_cap) {
+    dfree(b->d_pass);
+    b->pass_cap = std::max(npass, 2 * b->pass_cap);
+    CK(cudaMalloc(&b->d_pass, b->pass_cap * sizeof(BatchPass)));
+  }
+  if (nseg > b->seg_cap) {
+    dfree(b->d_seg);
+    b->seg_cap = std::max(nseg, 2 * b->seg_cap);
+    CK(cudaMalloc(&b->d_seg, b->seg_cap * sizeof(BatchSeg)));
+  }
+  if (nseg > b->done_cap) {
+    dfree(b->d_done);
+    b->done_cap = std::max(nseg, 2 * b->done_cap);
+    CK(cudaMalloc(&b->d_done, b->done_cap * sizeof(unsigned)));
+  }
+  return DSO_OK;
+}
+
+// The batch's tile line count for pass kinds of line length L staging SV
+// surfaces: the largest power of two G with SV G L <= 2048 amplitudes (one
+// 8-value slot per thread of a 256-thread CTA), at most the lines per surface.
+int batch_G(const dso_ctx* c, int L, int SV) {
+  const long long lines = c->P / L;
+  long long G = 1;
+  while (G * 2 <= lines && (long long)SV * G * 2 * L <= batch_max_tile_amplitudes()) G *= 2;
+  return (int)G;
+}
+
+dso_status batch_list(dso_ctx* c, const std::vector<Pass>& passes, std::vector<BatchPass>& out) {
+  out.clear();
+  for (const Pass& p : passes) {
+    BatchPass bp{};
+    long long ntiles = 0;
+    const cudaError_t e = build_pass_args(c, p, bp.a, ntiles);
+    if (e != cudaSuccess) return fail(DSO_EINVAL, std::string("batch pass arguments: ") + cudaGetErrorString(e));
+    bp.L = (int)c->nv[p.axis];
+    bp.log2L = ilog2(bp.L);
+    bp.SV = p.SV;
+    bp.ntiles = ntiles;
+    if ((long long)bp.SV * bp.a.G * bp.L > batch_max_tile_amplitudes())
+      return fail(DSO_EINVAL, "internal: a batch tile exceeds the kernel's tile");
+    out.push_back(bp);
+  }
+  return DSO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dso_status dso_batch_create(dso_batch** out, int device, int precision, void* cuda_stream) {
+  if (!out) return fail(DSO_EINVAL, "out is null");
+  *out = nullptr;
+  if (precision != DSO_FP64 && precision != DSO_FP32) return fail(DSO_EINVAL, "precision must be DSO_FP64 or DSO_FP32");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(DSO_ECUDA, "no CUDA device");
+  if (device < 0 || device >= ndev) return fail(DSO_EINVAL, "device index out of range");
+  DeviceGuard g(device);
+  dso_batch* b = new (std::nothrow) dso_batch();
+  if (!b) return fail(DSO_ENOMEM, "host allocation failed");
+  b->device = device;
+  b->prec = precision;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return fail(DSO_ECUDA, "stream creation failed");
+  } else {
+    b->own_stream = true;
+  }
+  if (cudaMalloc(&b->d_head, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream)) {
+    dfree(b->d_head);
+    dfree(b->d_err);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return fail(DSO_ENOMEM, "device allocation failed");
+  }
+  *out = b;
+  return DSO_OK;
+}
+
+void dso_batch_destroy(dso_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  dfree(b->d_pass);
+  dfree(b->d_seg);
+  dfree(b->d_done);
+  dfree(b->d_head);
+  dfree(b->d_err);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+dso_status dso_batch_add(dso_batch* b, dso_ctx* c, double t, double dt, int* slot) {
+  NvtxRange nvtx("dso_batch_add");
+  if (!b || !c || !slot) return fail(DSO_EINVAL, "null argument");
+  dso_status st = check_ready(c);
+  if (st != DSO_OK) return st;
+  if (c->device != b->device || c->prec != b->prec)
+    return fail(DSO_EINVAL, "the job's device and precision must be the batch's");
+  for (const BatchSlot& s2 : b->slots)
+    if (s2.live && s2.ctx == c) return fail(DSO_EINVAL, "the context is already in the batch");
+  if (!std::isfinite(t) || !std::isfinite(dt) || dt == 0.0) return fail(DSO_EINVAL, "t and dt must be finite, dt != 0");
+  const double ratio = t / dt, nr = std::round(ratio);
+  if (nr < 0 || std::fabs(ratio - nr) > 1e-9 * std::fmax(1.0, std::fabs(ratio)))
+    return fail(DSO_EINVAL, "t / dt must be a non-negative integer");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);  // the job's own work is done before the batch's stream takes over
+  const int ol = c->max_line, ot = c->max_tile;
+  c->max_line = kBatchMaxLine;
+  c->max_tile = kBatchMaxTile;
+  st = replan(c);
+  if (st != DSO_OK) {
+    c->max_line = ol;
+    c->max_tile = ot;
+    const dso_status back = replan(c);
+    (void)back;
+    return fail(DSO_EINVAL, "the job's grid is too large for a batch slot (lines of at most 1024 points, and "
+                            "S x 2048 points on axis 0, after one split): propagate it alone");
+  }
+  BatchSlot s;
+  try {
+    st = ensure_coeffs(c);
+    if (st == DSO_OK) st = ensure_tables(c, dt);
+    if (st != DSO_OK) return st;
+    for (int d = 0; d < c->Dv; ++d) {
+      c->G[d][0] = batch_G(c, (int)c->nv[d], 1);
+      c->G[d][1] = batch_G(c, (int)c->nv[d], c->S);
+      c->variant[d][0] = c->variant[d][1] = 0;
+    }
+    c->tuned = true;  // the batch's tile layout, not the autotuner's
+    drop_graph(c);
+    st = batch_list(c, step_passes(c, true), s.first);
+    if (st == DSO_OK) st = batch_list(c, step_passes(c, false), s.mid);
+    if (st == DSO_OK) st = batch_list(c, final_passes(c), s.fin);
+    if (st != DSO_OK) return st;
+  } catch (const std::exception& ex) {
+    return fail(DSO_EINVAL, ex.what());
+  }
+  s.ctx = c;
+  s.dt = dt;
+  s.steps_total = (long long)nr;
+  s.live = true;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (!b->slots[i].live && !b->slots[i].ctx) {
+      b->slots[i] = std::move(s);
+      *slot = (int)i;
+      return DSO_OK;
+    }
+  b->slots.push_back(std::move(s));
+  *slot = (int)b->slots.size() - 1;
+  return DSO_OK;
+}
+
+dso_status dso_batch_step(dso_batch* b, int* active) {
+  NvtxRange nvtx("dso_batch_step");
+  if (!b) return fail(DSO_EINVAL, "null batch");
+  DeviceGuard g(b->device);
+  // the work list: each unfinished job's passes for its next step (the
+  // first-step list, or a middle step's; the final passes after its last)
+  std::vector<BatchPass> passes;
+  std::vector<std::pair<int, int>> span;  // per running slot: first pass index, count
+  std::vector<int> running;
+  for (size_t i = 0; i < b->slots.size(); ++i) {
+    BatchSlot& s = b->slots[i];
+    if (!s.live || s.steps_done >= s.steps_total) continue;
+    const int start = (int)passes.size();
+    const std::vector<BatchPass>& body = s.steps_done == 0 ? s.first : s.mid;
+    passes.insert(passes.end(), body.begin(), body.end());
+    if (s.steps_done + 1 == s.steps_total) passes.insert(passes.end(), s.fin.begin(), s.fin.end());
+    span.emplace_back(start, (int)passes.size() - start);
+    running.push_back((int)i);
+  }
+  int still = 0;
+  if (!running.empty()) {
+    // segments by round, then by job: a job's pass r - 1 precedes its pass r
+    std::vector<BatchSeg> segs;
+    std::vector<int> last_seg(span.size(), -1);
+    int rounds = 0;
+    for (auto& sp : span) rounds = std::max(rounds, sp.second);
+    long long item = 0;
+    size_t smem = 0;
+    for (int r = 0; r < rounds; ++r)
+      for (size_t j = 0; j < span.size(); ++j) {
+        if (r >= span[j].second) continue;
+        const int pi = span[j].first + r;
+        const BatchPass& bp = passes[pi];
+        BatchSeg sg;
+        sg.item0 = item;
+        sg.pass = pi;
+        sg.prev = last_seg[j];
+        last_seg[j] = (int)segs.size();
+        segs.push_back(sg);
+        item += bp.ntiles;
+        const int Wi = 1 << std::min(bp.a.stride_log2, bp.a.G_log2);
+        smem = std::max(smem, batch_tile_smem(bp.L, bp.SV, bp.a.G, Wi, b->prec == DSO_FP32));
+      }
+    CK(cudaStreamSynchronize(b->stream));  // the previous launch no longer reads the host copies
+    b->h_pass.swap(passes);
+    b->h_seg.swap(segs);
+    dso_status st = batch_reserve(b, b->h_pass.size(), b->h_seg.size());
+    if (st != DSO_OK) return st;
+    CK(cudaMemcpyAsync(b->d_pass, b->h_pass.data(), b->h_pass.size() * sizeof(BatchPass), cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaMemcpyAsync(b->d_seg, b->h_seg.data(), b->h_seg.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice,
+                       b->stream));
+    CK(cudaMemsetAsync(b->d_done, 0, b->h_seg.size() * sizeof(unsigned), b->stream));
+    CK(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), b->stream));
+    CK(launch_batch_worklist(b->prec == DSO_FP32, b->d_seg, (int)b->h_seg.size(), b->d_pass, item, b->d_head,
+                             b->d_done, b->d_err, smem, b->stream));
+    b->launches += 1;
+    for (int i : running) b->slots[i].steps_done += 1;
+  }
+  for (const BatchSlot& s : b->slots)
+    if (s.live && s.steps_done < s.steps_total) ++still;
+  if (active) *active = still;
+  return DSO_OK;
+}
+
+dso_status dso_batch_sync(dso_batch* b) {
+  if (!b) return fail(DSO_EINVAL, "null batch");
+  DeviceGuard g(b->device);
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  if (h != 0) {
+    CK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream));
+    return fail(DSO_ETIMEOUT, "a batch tile's bounded wait for its job's previous pass gave up (code " +
+                                  std::to_string(h) + ")");
+  }
+  return DSO_OK;
+}
+
+dso_status dso_batch_slot_status(const dso_batch* b, int slot, int64_t* steps_done, int64_t* steps_total) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].live) return fail(DSO_EINVAL, "no such slot");
+  if (steps_done) *steps_done = b->slots[slot].steps_done;
+  if (steps_total) *steps_total = b->slots[slot].steps_total;
+  return DSO_OK;
+}
+
+dso_status dso_batch_retire(dso_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].live) return fail(DSO_EINVAL, "no such slot");
+  DeviceGuard g(b->device);
+  CK(cudaStreamSynchronize(b->stream));  // the job's state is final before its context is handed back
+  BatchSlot& s = b->slots[slot];
+  s.ctx->tuned = false;  // used alone again, the context tunes its own tiles
+  s.ctx->have_psi = true;
+  s.live = false;
+  s.ctx = nullptr;
+  s.first.clear();
+  s.mid.clear();
+  s.fin.clear();
+  return DSO_OK;
+}
+
+int64_t dso_batch_launch_count(const dso_batch* b) { return b ? b->launches : 0; }
 
 const char* dso_last_error(void) { return g_err.c_str(); }
 

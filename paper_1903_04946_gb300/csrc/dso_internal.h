@@ -94,6 +94,25 @@ cudaError_t launch_axis_pass_sv3(int L, int variant, const PassArgs& a, long lon
 cudaError_t launch_axis_pass_sv4(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
                                  const TmaMaps* maps, cudaStream_t st);
 
+// Batch slots (batch.cu): one pass of one job, with the tile line count the
+// batch chose for it, and a segment of the launch's work list (one pass of
+// one job; its tiles are items item0 .. item0 + ntiles - 1; `prev` is the
+// segment of the job's previous pass in this launch, or -1).
+struct BatchPass {
+  PassArgs a;
+  int L, log2L, SV;
+  long long ntiles;
+};
+struct BatchSeg {
+  long long item0;
+  int pass;  // index into the launch's BatchPass table
+  int prev;
+};
+size_t batch_tile_smem(int L, int SV, int G, int Wi, bool fp32);
+int batch_max_tile_amplitudes();  // SV * G * L of one tile of the batch kernel
+cudaError_t launch_batch_worklist(bool fp32, const BatchSeg* segs, int nseg, const BatchPass* passes, long long total,
+                                  unsigned long long* head, unsigned* done, int* err, size_t smem, cudaStream_t st);
+
 // Operator tables (tables.cu).
 // Twiddles w_m = exp(-2 pi i m / L), m = 0..L-1, in the tangent form the
 // FFT stages use: (cos, sin / cos), computed on the host in long double and
