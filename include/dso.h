@@ -388,6 +388,10 @@ dso_status dso_batch_retire(dso_batch* batch, int slot);
 /* Launches of the work-list kernel this batch has issued. */
 int64_t dso_batch_launch_count(const dso_batch* batch);
 
+/* Non-blocking: 1 while the batch's launched work is pending, 0 when it has
+ * finished, a negative dso_status on error (as dso_busy). */
+int dso_batch_busy(const dso_batch* batch);
+
 /* Message for the last failed call on this thread (never NULL; valid until
  * the next call on this thread). */
 const char* dso_last_error(void);

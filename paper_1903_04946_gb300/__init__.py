@@ -30,7 +30,7 @@ EXPORTS = (
     "dso_composition_coefficients", "dso_set_norm_check", "dso_fp64_issue_rate", "dso_inner",
     "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer", "dso_set_pass_limits",
     "dso_batch_create", "dso_batch_destroy", "dso_batch_add", "dso_batch_step", "dso_batch_sync",
-    "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count",
+    "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count", "dso_batch_busy",
 )
 
 _lib = None
@@ -89,6 +89,7 @@ def load(path: str = LIB):
         "dso_batch_slot_status": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "dso_batch_retire": (i32, [vp, i32]),
         "dso_batch_launch_count": (i64, [vp]),
+        "dso_batch_busy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -357,6 +358,13 @@ def dso_batch_launch_count(batch) -> int:
     return int(load().dso_batch_launch_count(batch))
 
 
+def dso_batch_busy(batch) -> bool:
+    r = load().dso_batch_busy(batch)
+    if r < 0:
+        raise DSOError(r, "dso_batch_busy")
+    return r == 1
+
+
 class Batch:
     """Batch slots: Context objects join with their own t and dt, advance
     one composed step per launch, and leave when retired."""
@@ -381,6 +389,9 @@ class Batch:
 
     def status(self, slot):
         return dso_batch_slot_status(self.b, slot)
+
+    def busy(self) -> bool:
+        return dso_batch_busy(self.b)
 
     def retire(self, slot) -> "Context":
         dso_batch_retire(self.b, slot)

@@ -582,7 +582,10 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 // Tuning results are shared by every context of the process with the same
 // grid, surface count, batch, precision and elementary method, so that a
 // stream of jobs of one shape (a serving loop) tunes once.
-using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int>;
+// The key holds everything that fixes the pass kinds and their lines: the
+// grid, S (which with the pass limits fixes the virtual axes), the batch,
+// precision, elementary method and device.
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int>;
 struct TuneVal {
   int G[DSO_MAX_VAXES][2];
   int variant[DSO_MAX_VAXES][2];
@@ -592,7 +595,8 @@ std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
 
 TuneKey tune_key(const dso_ctx* c) {
-  return TuneKey(c->D, c->n[0], c->n[1], c->n[2], c->S, c->B, c->prec, c->elementary, c->device);
+  return TuneKey(c->D, c->n[0], c->n[1], c->n[2], c->S, c->B, c->prec, c->elementary, c->device, c->max_line,
+                 c->max_tile);
 }
 
 dso_status autotune_tiles(dso_ctx* c) {
@@ -1927,6 +1931,15 @@ dso_status dso_batch_retire(dso_batch* b, int slot) {
 }
 
 int64_t dso_batch_launch_count(const dso_batch* b) { return b ? b->launches : 0; }
+
+int dso_batch_busy(const dso_batch* b) {
+  if (!b) return fail(DSO_EINVAL, "null batch");
+  DeviceGuard g(b->device);
+  const cudaError_t e = cudaStreamQuery(b->stream);
+  if (e == cudaSuccess) return 0;
+  if (e == cudaErrorNotReady) return 1;
+  return fail(DSO_ECUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
+}
 
 const char* dso_last_error(void) { return g_err.c_str(); }
 

@@ -2,10 +2,16 @@
 
 Requests (a problem, a composition order, a final time and a step) arrive
 over time.  The loop keeps every admitted job's wavefunction, potential and
-operator tables resident on the device, admits waiting jobs as soon as their
-device-memory footprint fits the budget left by the jobs in flight, and
-advances every admitted job in chunks of time steps, each job on its own CUDA
-stream, so jobs admitted while others run overlap with them on the device.
+operator tables resident on the device and admits waiting jobs as soon as
+their device-memory footprint fits the budget left by the jobs in flight.
+Admitted jobs take a slot of one batch (dso_batch_*): each round, one launch
+of the batch's work-list kernel advances every slotted job by one composed
+step, whatever their grids, schemes and time steps, and jobs join and leave
+between rounds.  A job too large for a batch slot (it fills the GPU alone)
+advances instead in chunks of time steps on its own CUDA stream, overlapping
+with the batch; so does a job above `slot_max_points` points per surface,
+whose steps alone keep the GPU busy and would set the length of every round.
+With slots=False every job runs that way.
 Finished jobs are read back, their latency (finish - arrival) recorded, and
 their memory returned to the budget for the next admission.  A job can be
 cancelled at any time (`Server.cancel`): a waiting job is dropped, a running
@@ -32,7 +38,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (DSO_FP64, DSO_TRIPLE_JUMP, Context, dso_busy, dso_scheme_coefficients, dso_set_scheme)
+from . import (DSO_FP64, DSO_TRIPLE_JUMP, Batch, Context, DSOError, dso_busy, dso_scheme_coefficients,
+               dso_set_scheme)
 
 
 @dataclass
@@ -51,6 +58,7 @@ class Job:
     finished: float = -1.0
     footprint: int = 0
     cancelled: bool = False
+    slot: int = -1                 # batch slot, or -1 (runs alone on its stream)
     result: np.ndarray = field(default=None, repr=False)
     observables: tuple = field(default=None, repr=False)
 
@@ -80,7 +88,8 @@ def job_cost_seconds(job, rate=1.2e9) -> float:
 
 
 class Server:
-    def __init__(self, device=0, budget_bytes=None, chunk_steps=16, precision=DSO_FP64):
+    def __init__(self, device=0, budget_bytes=None, chunk_steps=16, precision=DSO_FP64, slots=True,
+                 slot_max_points=1 << 16):
         import torch
         self.device = device
         if budget_bytes is None:
@@ -92,6 +101,13 @@ class Server:
         self.chunk_steps = chunk_steps
         self.precision = precision
         self._cancel = set()
+        self.batch = Batch(device=device, precision=precision) if slots else None
+        # a round of the batch lasts as long as its largest job's step: jobs
+        # above this many points per surface, which keep the GPU busy alone,
+        # run on their own streams instead, so that they do not hold back
+        # the small jobs' steps
+        self.slot_max_points = slot_max_points
+        self.batch_launches = 0
 
     def cancel(self, jid):
         """Cancel job `jid`: dropped if waiting, retired without a result at
@@ -102,11 +118,20 @@ class Server:
         job.ctx = Context(device=self.device, precision=self.precision)
         job.ctx.load_problem(job.problem)
         dso_set_scheme(job.ctx.ctx, job.order, job.scheme)
+        job.slot = -1
+        if self.batch is not None and job.problem.points <= self.slot_max_points:
+            try:
+                job.slot = self.batch.add(job.ctx, job.t, job.dt)  # the whole run, one step per round
+            except DSOError:
+                job.slot = -1  # too large for a slot: runs alone on its own stream
         job.admitted = now
         self.used += job.footprint
         self.peak_used = max(self.peak_used, self.used)
 
     def _retire(self, job, now, keep=True):
+        if job.slot >= 0:
+            self.batch.retire(job.slot)
+            job.slot = -1
         if keep:
             job.result = job.ctx.psi()
             job.observables = job.ctx.observables()
@@ -157,8 +182,24 @@ class Server:
                 active.append(job)
             max_active = max(max_active, len(active))
             progressed = False
+            slotted = [j for j in active if j.slot >= 0]
+            if slotted and not self.batch.busy():
+                # a round of the batch: retire finished or cancelled slot jobs,
+                # then one launch advances every other one by a step
+                for job in slotted:
+                    job.steps_done = self.batch.status(job.slot)[0]
+                    if job.jid in self._cancel or job.steps_done >= job.steps_total:
+                        job.cancelled = job.jid in self._cancel and job.steps_done < job.steps_total
+                        self._retire(job, time.perf_counter() - t0, keep=not job.cancelled)
+                        active.remove(job)
+                        if logf:
+                            logf.write(self._log_line(job) + "\n")
+                if any(j.slot >= 0 for j in active):
+                    self.batch.step()
+                    self.batch_launches += 1
+                progressed = True
             for job in list(active):
-                if dso_busy(job.ctx.ctx):
+                if job.slot >= 0 or dso_busy(job.ctx.ctx):
                     continue
                 if job.jid in self._cancel:
                     job.cancelled = True
@@ -188,6 +229,7 @@ class Server:
         lat = np.array([j.finished - j.arrival for j in done]) if done else np.zeros(1)
         work = sum(j.problem.points * j.substeps * j.steps_total for j in done)
         return {"jobs": len(jobs), "cancelled": len(jobs) - len(done), "wall_seconds": wall,
+                "batch_launches": self.batch_launches,
                 "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
                 "throughput_grid_pts_substeps_per_s": work / wall, "max_concurrent_jobs": max_active,
@@ -240,11 +282,12 @@ def main():
     ap.add_argument("--max-points", type=int, default=1 << 21)
     ap.add_argument("--seed", type=int, default=1907)
     ap.add_argument("--log", default=None, help="JSON-lines file with one record per job")
+    ap.add_argument("--no-slots", action="store_true", help="every job on its own stream (no batch slots)")
     ap.add_argument("--sequential", action="store_true",
                     help="also run the same jobs one at a time (no overlap) for comparison")
     args = ap.parse_args()
     jobs = make_jobs(args.jobs, args.seed, args.load, args.max_points)
-    srv = Server(budget_bytes=int(args.budget_gb * 2 ** 30) if args.budget_gb else None)
+    srv = Server(budget_bytes=int(args.budget_gb * 2 ** 30) if args.budget_gb else None, slots=not args.no_slots)
     stats = srv.run(jobs, log=args.log)
     stats.update(load=args.load, seed=args.seed, max_points=args.max_points,
                  workload=f"seeded Poisson stream: D in {{1,2,3}}, 2^8..{args.max_points} points per surface, "

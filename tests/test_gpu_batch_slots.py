@@ -181,3 +181,16 @@ def test_mixed_batch_config_full_size_one_launch_per_step(dso):
             al.close()
             assert_parity(out, oracle_propagate(pr, 6, "suzuki", steps * dt, dt))
     batch.close()
+
+
+def test_tuning_cache_keeps_pass_limits_apart(dso):
+    # the same grid tuned under the batch's limits (a split 64 x 64 axis) and
+    # under the defaults (one 4096-point line): each context must use tiles of
+    # its own layout
+    pr = synth.random_coupled(97, (4096,), 2, extent=20.0)
+    for limits in ((1024, 2048), None, (1024, 2048)):
+        c = _ctx(dso, pr, 4, "triple_jump", "VTV", limits=limits)
+        c.propagate(0.4, 0.2)
+        out = c.psi()
+        c.close()
+        assert_parity(out, oracle_propagate(pr, 4, "triple_jump", 0.4, 0.2))

@@ -96,7 +96,7 @@ def test_scheduler_admission_cancellation_and_log(monkeypatch, tmp_path):
         j.t = j.dt * min(int(round(j.t / j.dt)), 30)
     fps = [serving.footprint_bytes(j.problem, j.order, j.scheme) for j in jobs]
     budget = 3 * max(fps)
-    srv = serving.Server(budget_bytes=budget, chunk_steps=4)
+    srv = serving.Server(budget_bytes=budget, chunk_steps=4, slots=False)
     srv.cancel(jobs[11].jid)
     running = jobs[2]
 
@@ -118,3 +118,74 @@ def test_scheduler_admission_cancellation_and_log(monkeypatch, tmp_path):
             continue
         assert j.steps_done == j.steps_total and j.result is not None
         assert recs[j.jid]["norm"] == 1.0 and recs[j.jid]["latency_s"] >= 0
+
+
+class _FakeBatch:
+    """Stands in for a batch: every step advances each unfinished slot by one
+    composed step and reports itself busy for a poll; jobs above 2^10 points
+    are refused (too large for a slot), so they take the per-job path."""
+
+    def __init__(self, device=0, precision=0):
+        self.slots, self.next, self.busy_polls, self.launches = {}, 0, 0, 0
+
+    def add(self, ctx, t, dt):
+        from paper_1903_04946_gb300 import DSOError
+        if ctx.pr.points > 1 << 10:
+            raise DSOError(-1, "dso_batch_add")
+        slot = self.next
+        self.next += 1
+        self.slots[slot] = [0, int(round(t / dt))]
+        return slot
+
+    def step(self):
+        for s in self.slots.values():
+            if s[0] < s[1]:
+                s[0] += 1
+        self.busy_polls = 1
+        self.launches += 1
+        return sum(1 for s in self.slots.values() if s[0] < s[1])
+
+    def busy(self):
+        if self.busy_polls > 0:
+            self.busy_polls -= 1
+            return True
+        return False
+
+    def status(self, slot):
+        return tuple(self.slots[slot])
+
+    def retire(self, slot):
+        del self.slots[slot]
+
+
+def test_scheduler_with_batch_slots(monkeypatch):
+    """Jobs that fit a slot advance one step per batch round; the others
+    fall back to their own chunked propagation; every job gets exactly its
+    steps, a job cancelled while in a slot leaves at a step boundary."""
+    from paper_1903_04946_gb300 import serving
+    monkeypatch.setattr(serving, "Context", _FakeContext)
+    monkeypatch.setattr(serving, "Batch", _FakeBatch)
+    monkeypatch.setattr(serving, "dso_busy", _fake_busy)
+    monkeypatch.setattr(serving, "dso_set_scheme", lambda *a, **k: None)
+    jobs = serving.make_jobs(n_jobs=16, seed=23, load=50.0, max_points=1 << 12)
+    for j in jobs:
+        j.t = j.dt * min(int(round(j.t / j.dt)), 12)
+    srv = serving.Server(budget_bytes=1 << 40, chunk_steps=5)
+    small = [j for j in jobs if j.problem.points <= 1 << 10]
+    big = [j for j in jobs if j.problem.points > 1 << 10]
+    assert small and big
+    victim = small[0]
+
+    def tick(server, now):
+        if victim.slot >= 0 and victim.steps_done >= 2:
+            server.cancel(victim.jid)
+
+    stats = srv.run(jobs, on_tick=tick)
+    assert _FakeContext.live == 0
+    assert victim.cancelled and victim.result is None and 2 <= victim.steps_done < victim.steps_total
+    for j in jobs:
+        if j is victim:
+            continue
+        assert j.steps_done == j.steps_total and j.result is not None, j.jid
+    # slotted jobs never took the per-job path
+    assert stats["batch_launches"] >= max(j.steps_total for j in small if j is not victim)
