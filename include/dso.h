@@ -61,7 +61,7 @@ typedef enum {
 
 enum { DSO_HOST = 0, DSO_DEVICE = 1 };
 enum { DSO_FP64 = 0, DSO_FP32 = 1 };
-enum { DSO_TRIPLE_JUMP = 0, DSO_SUZUKI = 1 };
+enum { DSO_TRIPLE_JUMP = 0, DSO_SUZUKI = 1, DSO_OPTIMAL = 2 };
 enum { DSO_VTV = 0, DSO_TVT = 1, DSO_VT = 2, DSO_TV = 3 };
 
 /* Limits of this build. */
@@ -113,7 +113,10 @@ dso_status dso_set_masses(dso_ctx* ctx, const double* m);
 dso_status dso_load_potential(dso_ctx* ctx, int S, const double* V, int where);
 
 /* Composition of Sec. II D-F: order in {2,4,6,8,10}; scheme DSO_TRIPLE_JUMP
- * or DSO_SUZUKI; elementary DSO_VTV (Eq. (so_VTV): the potential acts first
+ * or DSO_SUZUKI (recursive), or DSO_OPTIMAL for orders 6 and 8: the
+ * non-recursive 9- and 17-stage symmetric compositions of Kahan and Li that
+ * Table II lists as "optimal" (coefficients from the literature the paper
+ * cites, tabulated in the library); elementary DSO_VTV (Eq. (so_VTV): the potential acts first
  * and last, with the a~ coefficients) or DSO_TVT (Eq. (so_TVT): the kinetic
  * step acts first and last and takes the a~ coefficients, the potential the
  * b~); prune must be 1 (the coefficients of Eq.

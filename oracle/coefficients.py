@@ -32,6 +32,23 @@ getcontext().prec = 60
 
 TRIPLE_JUMP = "triple_jump"
 SUZUKI = "suzuki"
+OPTIMAL = "optimal"
+
+# The "optimal" compositions of Sec. II D (Table II's last rows) are not
+# recursive: their coefficients come from a numerical optimisation in the
+# literature the paper cites (Kahan and Li, Math. Comp. 66, 1089 (1997)):
+# 9 stages for order 6 and 17 for order 8, symmetric.  Only the first half and
+# the middle coefficient are listed (gamma_1 .. gamma_{(M+1)/2}), to 20
+# significant digits.  They satisfy the consistency and power-sum order
+# conditions to that precision, and the propagation tests measure their
+# convergence order.
+OPTIMAL_HALF = {
+    6: ("0.39216144400731413928", "0.33259913678935943860", "-0.70624617255763935981",
+        "0.082213596293550800230", "0.79854399093482996340"),
+    8: ("0.13020248308889008088", "0.56116298177510838456", "-0.38947496264484728641",
+        "0.15884190655515560090", "-0.39590389413323757734", "0.18453964097831570709",
+        "0.25837438768632204729", "0.29501172360931029887", "-0.60550853383003451170"),
+}
 
 
 def gamma_triple_jump(p: int):
@@ -54,9 +71,15 @@ def gamma_suzuki(p: int):
 def composition(order: int, scheme: str):
     """Elementary-step coefficients gamma (time order) of the recursive
     composition of a second-order method up to ``order`` (Sec. II D):
-    U_{p+2}(dt) = U_p(gamma_M dt) ... U_p(gamma_1 dt)."""
+    U_{p+2}(dt) = U_p(gamma_M dt) ... U_p(gamma_1 dt); for the OPTIMAL scheme
+    the tabulated non-recursive coefficients above."""
     if order < 2 or order % 2:
         raise ValueError("order must be even and >= 2")
+    if scheme == OPTIMAL:
+        if order not in OPTIMAL_HALF:
+            raise ValueError("the optimal compositions are available for orders 6 and 8")
+        half = [Decimal(x) for x in OPTIMAL_HALF[order]]
+        return half[:-1] + [half[-1]] + half[:-1][::-1]
     if scheme not in (TRIPLE_JUMP, SUZUKI):
         raise ValueError(f"unknown scheme {scheme!r}")
     seq = [Decimal(1)]

@@ -19,7 +19,8 @@ from .build import LIB, build  # noqa: F401
 DSO_OK, DSO_EINVAL, DSO_ENOMEM, DSO_ECUDA, DSO_ESTATE, DSO_ETIMEOUT, DSO_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 DSO_HOST, DSO_DEVICE = 0, 1
 DSO_FP64, DSO_FP32 = 0, 1
-DSO_TRIPLE_JUMP, DSO_SUZUKI = 0, 1
+DSO_TRIPLE_JUMP, DSO_SUZUKI, DSO_OPTIMAL = 0, 1, 2
+SCHEME_CODES = {"triple_jump": DSO_TRIPLE_JUMP, "suzuki": DSO_SUZUKI, "optimal": DSO_OPTIMAL}
 DSO_VTV, DSO_TVT, DSO_VT, DSO_TV = 0, 1, 2, 3
 
 EXPORTS = (

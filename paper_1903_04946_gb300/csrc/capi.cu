@@ -953,7 +953,10 @@ dso_status dso_set_scheme(dso_ctx* c, int order, int scheme, int elementary, int
     scheme = DSO_TRIPLE_JUMP;
   } else {
     if (order < 2 || order > 10 || order % 2) return fail(DSO_EINVAL, "order must be 2, 4, 6, 8 or 10");
-    if (scheme != DSO_TRIPLE_JUMP && scheme != DSO_SUZUKI) return fail(DSO_EINVAL, "unknown scheme");
+    if (scheme != DSO_TRIPLE_JUMP && scheme != DSO_SUZUKI && scheme != DSO_OPTIMAL)
+      return fail(DSO_EINVAL, "unknown scheme");
+    if (scheme == DSO_OPTIMAL && order != 6 && order != 8)
+      return fail(DSO_EINVAL, "the optimal compositions have orders 6 and 8");
     if (elementary != DSO_VTV && elementary != DSO_TVT)
       return fail(DSO_EINVAL, "elementary must be DSO_VTV, DSO_TVT, DSO_VT or DSO_TV");
   }

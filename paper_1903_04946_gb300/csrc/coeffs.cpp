@@ -14,8 +14,15 @@
 // Repeated values are found on the first half of the symmetric sequence and
 // mirrored (Eq. (range_index_unq), indices 0-based here).
 //
+// The "optimal" compositions of Sec. II D (Table II's last rows) are not
+// recursive: they take the 9-stage (order 6) and 17-stage (order 8)
+// symmetric coefficients that Kahan and Li (Math. Comp. 66, 1089 (1997))
+// obtained by numerical optimisation, listed below to 20 significant digits
+// (first half and middle coefficient).
+//
 // Arithmetic is in long double; values are rounded to double once.
 #include <cmath>
+#include <cstdlib>
 #include <stdexcept>
 
 #include "dso_internal.h"
@@ -58,6 +65,24 @@ void find_unique(const std::vector<long double>& v, std::vector<double>& uniq, s
   for (long double x : u) uniq.push_back((double)x);
 }
 
+// First half and middle of the optimal compositions (time order).
+const char* const kOptimal6[] = {"0.39216144400731413928", "0.33259913678935943860", "-0.70624617255763935981",
+                                 "0.082213596293550800230", "0.79854399093482996340"};
+const char* const kOptimal8[] = {"0.13020248308889008088", "0.56116298177510838456", "-0.38947496264484728641",
+                                 "0.15884190655515560090", "-0.39590389413323757734", "0.18453964097831570709",
+                                 "0.25837438768632204729", "0.29501172360931029887", "-0.60550853383003451170"};
+
+std::vector<long double> optimal_gamma(int order) {
+  const char* const* half = order == 6 ? kOptimal6 : kOptimal8;
+  const int nh = order == 6 ? 5 : 9;
+  std::vector<long double> h;
+  for (int k = 0; k < nh; ++k) h.push_back(strtold(half[k], nullptr));
+  std::vector<long double> g(h.begin(), h.end() - 1);
+  g.push_back(h.back());
+  for (int k = nh - 2; k >= 0; --k) g.push_back(h[k]);
+  return g;
+}
+
 }  // namespace
 
 Coeffs coefficients_from_gammas(const std::vector<long double>& g) {
@@ -95,6 +120,10 @@ Coeffs build_coefficients(int order, int scheme) {
     return c;
   }
   if (order < 2 || order % 2 != 0 || order > 10) throw std::invalid_argument("order must be 1, 2, 4, 6, 8 or 10");
+  if (scheme == 2) {
+    if (order != 6 && order != 8) throw std::invalid_argument("the optimal compositions have orders 6 and 8");
+    return coefficients_from_gammas(optimal_gamma(order));
+  }
   if (scheme != 0 && scheme != 1) throw std::invalid_argument("unknown composition scheme");
   std::vector<long double> g{1.0L};
   for (int p = 2; p < order; p += 2) {

@@ -26,14 +26,14 @@ import time
 
 import numpy as np
 
-from . import (DSO_SUZUKI, DSO_TRIPLE_JUMP, Context, dso_scheme_coefficients, dso_set_scheme)
+from . import (SCHEME_CODES, Context, dso_scheme_coefficients, dso_set_scheme)
 
 SCHEMES = [("triple_jump", 2), ("triple_jump", 4), ("triple_jump", 6), ("triple_jump", 8), ("triple_jump", 10),
-           ("suzuki", 4), ("suzuki", 6), ("suzuki", 8), ("suzuki", 10)]
+           ("suzuki", 4), ("suzuki", 6), ("suzuki", 8), ("suzuki", 10), ("optimal", 6), ("optimal", 8)]
 
 
 def _code(scheme):
-    return DSO_SUZUKI if scheme == "suzuki" else DSO_TRIPLE_JUMP
+    return SCHEME_CODES[scheme]
 
 
 def _timed_run(ctx, tf, dt):
@@ -171,6 +171,51 @@ def study(grid=32, batch=32, tf=2000.0, target=1e-10, kmax=20, ref_k=7, seed=190
                                                         / best_b["batch_per_wavepacket_seconds"])
         if o2:
             out["best_vs_order2_speedup"] = o2["single_seconds"] / best["single_seconds"]
+    return out
+
+
+def time_to_target(problem, schemes, tf=2000.0, target=1e-10, ref=("suzuki", 10, 12), kmax=24, kmax_by_order=None):
+    """Time to `target` of single-job propagations of `problem` to tf, one
+    entry per (scheme, order) of `schemes`: dt = tf / 2^k from the order's
+    predicted k (from the first error, e ~ C dt^order) upward until the
+    error against the reference (ref = (scheme, order, k) and its own run at
+    2 dt, whose difference is reported) is <= target.  A method that has not
+    reached the target by k = kmax_by_order[order] (default kmax) is not run
+    further: its time at the k that its last two errors predict is
+    extrapolated from the last run (time proportional to the steps), and the
+    entry says so.  Returns one dict per method and the reference's error
+    bound."""
+    rs, ro, rk = ref
+    ref_psi, _ = _propagate([problem], rs, ro, tf, rk, False)
+    ref_c, _ = _propagate([problem], rs, ro, tf, rk - 1, False)
+    out = {"reference": {"scheme": rs, "order": ro, "dt": tf / 2 ** rk,
+                         "error_of_run_at_2dt": _err(problem, ref_c, ref_psi)}, "methods": []}
+    for scheme, order in schemes:
+        nsub = len(dso_scheme_coefficients(order, _code(scheme))[1])
+        k = {2: 8, 4: 6, 6: 5, 8: 4, 10: 3}[order]
+        row = {"scheme": scheme, "order": order, "substeps_per_step": nsub, "reached": False}
+        tried = 0
+        top = (kmax_by_order or {}).get(order, kmax)
+        seen = []
+        while tried < 8:
+            psi, secs = _propagate([problem], scheme, order, tf, k, False)
+            e = _err(problem, psi, ref_psi)
+            tried += 1
+            seen.append((k, e, secs))
+            if e <= target:
+                row.update(reached=True, k=k, dt=tf / 2 ** k, steps=2 ** k, error=e, seconds=secs)
+                break
+            step = 2 if (not np.isfinite(e) or e > 1.0) else max(1, int(np.ceil(np.log2(e / target) / order)))
+            if k + step > top:
+                if len(seen) >= 2 and seen[-2][1] > e > 0:  # fitted order from the last two runs
+                    (k0, e0, _), (k1, e1, s1) = seen[-2], seen[-1]
+                    p = np.log2(e0 / e1) / (k1 - k0)
+                    kx = k1 + int(np.ceil(np.log2(e1 / target) / p))
+                    row.update(extrapolated=True, fitted_order=float(p), k=kx, dt=tf / 2 ** kx, steps=2 ** kx,
+                               seconds=s1 * 2.0 ** (kx - k1), last_run={"k": k1, "error": e1, "seconds": s1})
+                break
+            k += step
+        out["methods"].append(row)
     return out
 
 

@@ -21,7 +21,7 @@ import json
 
 import numpy as np
 
-from . import DSO_SUZUKI, DSO_TRIPLE_JUMP, Context
+from . import SCHEME_CODES, Context
 
 
 def wrap(x):
@@ -32,7 +32,7 @@ def wrap(x):
 def phases(problem, order, scheme, tf, k, device=0):
     """(indices, phases) per surface after propagating to tf with dt = tf / 2^k."""
     ctx = Context(problem, device=device, order=order,
-                  scheme=DSO_SUZUKI if scheme == "suzuki" else DSO_TRIPLE_JUMP)
+                  scheme=SCHEME_CODES[scheme])
     try:
         ctx.propagate(tf, tf / 2 ** k)
         return ctx.phase_at_density_maximum()

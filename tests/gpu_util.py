@@ -17,7 +17,7 @@ def require_gpu():
 
 def gpu_propagate(problem, order, scheme, t, dt, psi=None, elementary="VTV", fp32=False):
     import paper_1903_04946_gb300 as dso
-    sch = dso.DSO_SUZUKI if scheme == "suzuki" else dso.DSO_TRIPLE_JUMP
+    sch = dso.SCHEME_CODES[scheme]
     el = {"VTV": dso.DSO_VTV, "TVT": dso.DSO_TVT, "VT": dso.DSO_VT, "TV": dso.DSO_TV}[elementary]
     ctx = dso.Context(problem, order=order, scheme=sch, elementary=el,
                       precision=dso.DSO_FP32 if fp32 else dso.DSO_FP64)

@@ -42,7 +42,7 @@ def _mixed_jobs():
 
 
 def _ctx(dso, pr, order, scheme, el, limits=None):
-    sch = dso.DSO_SUZUKI if scheme == "suzuki" else dso.DSO_TRIPLE_JUMP
+    sch = dso.SCHEME_CODES[scheme]
     elc = {"VTV": dso.DSO_VTV, "TVT": dso.DSO_TVT}[el]
     ctx = dso.Context(pr, order=order, scheme=sch, elementary=elc)
     if limits:

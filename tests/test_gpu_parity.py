@@ -200,3 +200,16 @@ def test_long_1d_grids(dso, N, S, el):
     ref = oracle_propagate(pr, 4, "suzuki", 3 * dt, dt, elementary=el)
     out = gpu_propagate(pr, 4, "suzuki", 3 * dt, dt, elementary=el)
     assert_parity(out, ref)
+
+
+# -- the "optimal" non-recursive compositions of orders 6 and 8 (Table II)
+@pytest.mark.parametrize("order", [6, 8])
+def test_optimal_compositions_parity(dso, order):
+    pr = synth.pyrazine_like(seed=41, n=(16, 32, 8))
+    ref = oracle_propagate(pr, order, "optimal", 80.0, 40.0)
+    out = gpu_propagate(pr, order, "optimal", 80.0, 40.0)
+    assert_parity(out, ref)
+    nai = synth.nai_like()
+    ref = oracle_propagate(nai, order, "optimal", 200.0, 10.0)
+    out = gpu_propagate(nai, order, "optimal", 200.0, 10.0)
+    assert_parity(out, ref)

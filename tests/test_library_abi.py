@@ -59,7 +59,7 @@ def _table2():
 @pytest.mark.parametrize("row", _table2(), ids=lambda r: f"{r[0]}{r[1]}")
 def test_library_coefficients_match_table2(lib, row):
     sch, order, after, na, nb = row
-    scheme = dso.DSO_SUZUKI if sch == "suzuki" else dso.DSO_TRIPLE_JUMP
+    scheme = dso.SCHEME_CODES.get(sch, dso.DSO_TRIPLE_JUMP)
     a, b, ia, ib, nau, nbu = dso.dso_scheme_coefficients(order, scheme)
     assert len(a) + len(b) == after
     assert (nau, nbu) == (na, nb)
@@ -135,3 +135,13 @@ def test_composition_coefficients_from_gammas(lib):
 def test_composition_rejects_bad_gammas(lib, bad):
     with pytest.raises(dso.DSOError):
         dso.dso_composition_coefficients(bad)
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_library_optimal_coefficients_match_oracle(lib, order):
+    a, b, ia, ib, nau, nbu = dso.dso_scheme_coefficients(order, dso.DSO_OPTIMAL)
+    sp = C.Splitting(order, C.OPTIMAL)
+    assert np.allclose(a, sp.a, rtol=0, atol=1e-15) and np.allclose(b, sp.b, rtol=0, atol=1e-15)
+    assert list(ia) == sp.Ia and list(ib) == sp.Ib
+    with pytest.raises(dso.DSOError):
+        dso.dso_scheme_coefficients(4, dso.DSO_OPTIMAL)

@@ -24,7 +24,8 @@ def _table2():
 @pytest.mark.parametrize("row", _table2(), ids=lambda r: f"{r[0]}{r[1]}")
 def test_table2_counts(row):
     sch, order, before, after, na, nb = row
-    sp = C.Splitting(order, C.TRIPLE_JUMP if sch in ("elementary", "triple_jump") else C.SUZUKI)
+    sp = C.Splitting(order, {"elementary": C.TRIPLE_JUMP, "triple_jump": C.TRIPLE_JUMP, "suzuki": C.SUZUKI,
+                             "optimal": C.OPTIMAL}[sch])
     assert sp.n_actions_before == before
     assert sp.n_actions_after == after
     assert len(sp.a_unq_dec) == na
@@ -133,3 +134,20 @@ def test_explicit_gammas_reproduce_the_recursive_schemes(order, scheme):
     assert len(sp.a) == len(ref.a) and len(sp.b) == len(ref.b)
     assert max(abs(x - y) for x, y in zip(sp.a + sp.b, ref.a + ref.b)) < 1e-14
     assert sp.Ia == ref.Ia and sp.Ib == ref.Ib
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_optimal_compositions_order_conditions(order):
+    """Consistency and the power-sum conditions sum gamma^k = 0 for odd
+    k = 3..order-1 that every symmetric composition of a symmetric
+    second-order method of this order must meet (the other order conditions
+    are checked by the measured convergence order in the propagation tests);
+    symmetric and of the stage counts of Table II (9 and 17)."""
+    g = C.composition(order, C.OPTIMAL)
+    assert len(g) == {6: 9, 8: 17}[order]
+    assert all(g[k] == g[-1 - k] for k in range(len(g)))
+    assert abs(sum(g) - 1) < Decimal("1e-19")
+    for k in range(3, order, 2):
+        assert abs(sum(x ** k for x in g)) < Decimal("1e-18"), k
+    # the next power sum is not zero: the order is not higher by accident
+    assert abs(sum(x ** (order + 1) for x in g)) > Decimal("1e-4")

@@ -16,7 +16,7 @@ import pytest
 
 import synth
 from oracle import brute, observables as O, propagate as P
-from oracle.coefficients import SUZUKI, TRIPLE_JUMP
+from oracle.coefficients import OPTIMAL, SUZUKI, TRIPLE_JUMP
 
 
 def _problem_1d(V, psi0, n, qmin, qmax, mass):
@@ -105,6 +105,8 @@ def _harmonic_case():
     (4, TRIPLE_JUMP, P.VTV, (0.2, 0.1)),
     (4, SUZUKI, P.VTV, (0.4, 0.2)),
     (6, TRIPLE_JUMP, P.VTV, (0.4, 0.2)),
+    (6, OPTIMAL, P.VTV, (0.4, 0.2)),
+    (8, OPTIMAL, P.VTV, (1.0, 0.5)),
 ])
 def test_harmonic_coherent_state_convergence_order(order, scheme, elementary, dts):
     pr, exact = _harmonic_case()
@@ -139,6 +141,19 @@ def test_brute_force_limit_and_order(order, scheme, elementary):
     assert abs(slope - order) < 0.35, (errs, slope)
     fine = P.propagate(pr, t, 1 / 64, 8, SUZUKI, elementary)
     assert O.l2_error(pr, fine, ref) < 1e-11
+
+
+@pytest.mark.parametrize("order,dts", [(6, (0.1, 0.05)), (8, (0.125, 0.0625))])
+def test_optimal_compositions_order_on_an_anharmonic_problem(order, dts):
+    """The tabulated optimal compositions reach their order on a coupled,
+    anharmonic grid problem, where every order condition counts (on a
+    quadratic Hamiltonian some of them coincide), against dense exp(-iHt)."""
+    pr = _tiny()
+    t = 1.0
+    ref = brute.exact_propagate(pr, pr.psi0, t)
+    errs = [O.l2_error(pr, P.propagate(pr, t, dt, order, OPTIMAL), ref) for dt in dts]
+    slope = np.log2(errs[0] / errs[1])
+    assert abs(slope - order) < 0.35, (errs, slope)
 
 
 def test_brute_force_2d_three_surfaces():
