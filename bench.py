@@ -223,16 +223,17 @@ def kind_name(k):
 # GPU arm
 # --------------------------------------------------------------------------
 
+KERNEL_SOURCES = ("axis_pass.cuh", "axis_pass_pq.cuh", "axis_pass_tma.cuh", "pass_args.h", "pass_launch.cuh")
+
+
 def kernel_sources_hash() -> str:
     """First 16 hex digits of the SHA-256 over the device code of the axis
-    passes (csrc/*.cuh and their argument struct csrc/pass_args.h, in name
-    order, each prefixed by its base name)."""
-    import glob
+    passes the benchmark times (KERNEL_SOURCES in csrc/, in name order, each
+    prefixed by its base name)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1903_04946_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cuh")) + [os.path.join(csrc, "pass_args.h")],
-                    key=os.path.basename):
+    for f in sorted((os.path.join(csrc, n) for n in KERNEL_SOURCES), key=os.path.basename):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

@@ -335,8 +335,13 @@ dso_status dso_fp64_issue_rate(int device, double* inst_per_s);
  * potential is loaded (the state is kept), else at dso_load_potential.  A
  * context added to a batch gets the batch's limits (1024, 2048); setting the
  * same limits on a context that propagates alone gives it the batch's pass
- * layout, so that the two give bitwise the same result.  The paper has no
- * counterpart. */
+ * layout, so that the two give bitwise the same result.  Without this call,
+ * a 1-D grid that the default limits keep as one line (S n <= 8192) has its
+ * limits chosen by timing a step under a few candidates at its first
+ * propagation (one line keeps a small job on one SM; a split spreads it over
+ * many), cached for the process per grid, S, precision and elementary method
+ * (not per batch size, so a batch and its jobs alone share the layout).  The
+ * paper has no counterpart. */
 dso_status dso_set_pass_limits(dso_ctx* ctx, int max_line, int max_tile);
 
 /* Batch slots (continuous batching).  A batch advances many jobs -- each a

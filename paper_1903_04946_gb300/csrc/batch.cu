@@ -33,6 +33,14 @@ namespace {
 
 constexpr int kBatchWaitPolls = 1 << 24;  // with a 128 ns back-off: a few seconds
 
+// Resident CTAs per SM the register allocation must allow: 4 (64 registers;
+// 144 bytes of spills per thread in FP64, none in FP32).  Measured on the
+// 544-job batching mix: 0.657 s per 10 steps with 2 (124 registers, no
+// spills), 0.582 s with 3, 0.575 s with 4.
+#ifndef DSO_BATCH_MIN_BLOCKS
+#define DSO_BATCH_MIN_BLOCKS 4
+#endif
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -43,9 +51,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // CTA starts (not by blockIdx, so that items are taken in order by running
 // CTAs only).  A persistent loop over items would let the compiler keep the
 // loop-invariant shared-memory addresses of every FFT stage live across
-// items: over 250 registers with spills, against 124 without spills here.
+// items: over 250 registers with spills; here the register count is set by
+// the occupancy bound below.
 template <typename C>
-__global__ void __launch_bounds__(kRtThreads, 2) batch_worklist_kernel(const BatchSeg* __restrict__ segs, int nseg,
+__global__ void __launch_bounds__(kRtThreads, DSO_BATCH_MIN_BLOCKS) batch_worklist_kernel(const BatchSeg* __restrict__ segs, int nseg,
                                                                      const BatchPass* __restrict__ passes,
                                                                      long long total,
                                                                      unsigned long long* __restrict__ head,

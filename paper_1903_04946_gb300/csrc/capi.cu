@@ -158,6 +158,8 @@ struct dso_ctx {
   int wait_probe = 0;        // dso_set_wait_probe: polls of the TMA variant's diagnostic wait (0: off)
   int max_line = DSO_MAX_LINE;  // dso_set_pass_limits: longest pass line,
   int max_tile = 8192;          // and most points of the S surfaces of an axis-0 line
+  bool limits_user = false;     // limits set by the caller: not tuned
+  bool limits_tuned = false;    // limits chosen by timing (small 1-D grids)
   unsigned* queue = nullptr;  // tile queue of the persistent variant (2 counters)
   int* err = nullptr;         // set by kernels whose bounded waits gave up
   bool tuned = false;
@@ -746,6 +748,93 @@ dso_status autotune_tiles(dso_ctx* c) {
   return DSO_OK;
 }
 
+// Pass limits of small 1-D grids.  Unsplit, a 1-D grid of n <= 4096 points
+// is one line: one CTA per job and surface set, so a small job runs on one
+// SM (about 49 us per step for 1024 points and two surfaces, bound by that
+// SM's FP64 pipe).  Split into two virtual axes (four-step), every pass has
+// tens of lines and spreads over as many SMs, at the cost of a second pass
+// and the twiddles.  For 1-D grids whose default plan is one line (S n <=
+// 8192) the first propagation times a middle step under each candidate
+// limit on a copy of psi and keeps the fastest.  The choice is cached per
+// grid, surfaces, precision, elementary method and device -- not per batch
+// size, so that a batch of such jobs and each job alone use the same layout
+// and give bitwise the same result.  Skipped when the caller set the limits
+// or forces a plan (DSO_PLAN).
+using LimitsKey = std::tuple<int64_t, int, int, int, int>;
+std::mutex g_limits_mu;
+std::map<LimitsKey, std::pair<int, int>> g_limits_cache;
+
+dso_status tune_limits(dso_ctx* c, double dt) {
+  c->limits_tuned = true;
+  if (c->limits_user || getenv("DSO_PLAN") || c->D != 1) return DSO_OK;
+  if ((long long)c->S * c->n[0] > 8192) return DSO_OK;  // already split by default
+  const char* env = getenv("DSO_AUTOTUNE");
+  if (env && env[0] == '0') return DSO_OK;
+  const LimitsKey key(c->n[0], c->S, c->prec, c->elementary, c->device);
+  {
+    std::lock_guard<std::mutex> lock(g_limits_mu);
+    auto it = g_limits_cache.find(key);
+    if (it != g_limits_cache.end()) {
+      if (it->second.first != c->max_line || it->second.second != c->max_tile) {
+        c->max_line = it->second.first;
+        c->max_tile = it->second.second;
+        return replan(c);
+      }
+      return DSO_OK;
+    }
+  }
+  static const int cand[][2] = {{DSO_MAX_LINE, 8192}, {256, 512}, {128, 256}, {64, 128}, {32, 64}};
+  const size_t bytes = (size_t)c->B * c->S * c->P * c->esz();
+  if (!c->work) CK(cudaMalloc(&c->work, bytes));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t err = cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bl = c->max_line, bt = c->max_tile;
+  for (const auto& cd : cand) {
+    if (err != cudaSuccess) break;
+    c->max_line = cd[0];
+    c->max_tile = cd[1];
+    if (replan(c) != DSO_OK) continue;  // the grid does not fit these limits
+    dso_status st = ensure_tables(c, dt);
+    if (st == DSO_OK) st = autotune_tiles(c);
+    if (st != DSO_OK) {
+      err = cudaErrorUnknown;
+      break;
+    }
+    err = cudaMemcpyAsync(c->work, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    void* keep = c->psi;
+    c->psi = c->work;
+    const std::vector<Pass> mid = step_passes(c, false);
+    for (const Pass& p : mid)  // warm-up
+      if (err == cudaSuccess) err = run_pass(c, p);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 10 && err == cudaSuccess; ++r)
+      for (const Pass& p : mid)
+        if (err == cudaSuccess) err = run_pass(c, p);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    c->psi = keep;
+    if (err == cudaSuccess && ms < best) {
+      best = ms;
+      bl = cd[0];
+      bt = cd[1];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  CK(err);
+  c->max_line = bl;
+  c->max_tile = bt;
+  dso_status st = replan(c);
+  if (st != DSO_OK) return st;
+  std::lock_guard<std::mutex> lock(g_limits_mu);
+  g_limits_cache[key] = {bl, bt};
+  return DSO_OK;
+}
+
 dso_status ensure_step_graph(dso_ctx* c) {
   if (c->step_exec) return DSO_OK;
   std::vector<Pass> passes = step_passes(c, false);
@@ -854,6 +943,11 @@ dso_status dso_set_grid(dso_ctx* c, int D, const int64_t* n, const double* qmin,
   c->have_grid = true;
   c->have_mass = false;
   c->B = 1;
+  c->limits_tuned = false;  // a new grid: chosen again at the first propagation
+  if (!c->limits_user) {
+    c->max_line = DSO_MAX_LINE;
+    c->max_tile = 8192;
+  }
   return DSO_OK;
 }
 
@@ -865,6 +959,7 @@ dso_status dso_set_batch(dso_ctx* c, int B) {
   cudaStreamSynchronize(c->stream);
   drop_model(c);
   c->B = B;
+  c->limits_tuned = false;
   return DSO_OK;
 }
 
@@ -896,6 +991,7 @@ dso_status dso_load_potential(dso_ctx* c, int S, const double* V, int where) {
   cudaStreamSynchronize(c->stream);
   drop_model(c);
   c->S = S;
+  c->limits_tuned = false;
   CK(cudaMalloc(&c->V, count * sizeof(double)));
   CK(cudaMemcpyAsync(c->V, V, count * sizeof(double), where == DSO_HOST ? cudaMemcpyHostToDevice
                                                                          : cudaMemcpyDeviceToDevice, c->stream));
@@ -1271,6 +1367,10 @@ dso_status dso_propagate(dso_ctx* c, double t, double dt) {
   try {
     st = ensure_coeffs(c);
     if (st != DSO_OK) return st;
+    if (!c->limits_tuned) {
+      st = tune_limits(c, dt);
+      if (st != DSO_OK) return st;
+    }
     st = ensure_tables(c, dt);
     if (st != DSO_OK) return st;
     if (!c->tuned) {
@@ -1618,6 +1718,7 @@ dso_status dso_set_pass_limits(dso_ctx* c, int max_line, int max_tile) {
   const int ol = c->max_line, ot = c->max_tile;
   c->max_line = max_line;
   c->max_tile = max_tile;
+  c->limits_user = true;
   if (c->have_V) {  // S is known: plan again (psi is in the position representation: unaffected)
     const dso_status st = replan(c);
     if (st != DSO_OK) {
@@ -1789,6 +1890,7 @@ dso_status dso_batch_add(dso_batch* b, dso_ctx* c, double t, double dt, int* slo
   const int ol = c->max_line, ot = c->max_tile;
   c->max_line = kBatchMaxLine;
   c->max_tile = kBatchMaxTile;
+  c->limits_tuned = true;  // the batch's limits, not tuned ones
   st = replan(c);
   if (st != DSO_OK) {
     c->max_line = ol;

@@ -206,15 +206,15 @@ def time_to_target(problem, schemes, tf=2000.0, target=1e-10, ref=("suzuki", 10,
                 row.update(reached=True, k=k, dt=tf / 2 ** k, steps=2 ** k, error=e, seconds=secs)
                 break
             step = 2 if (not np.isfinite(e) or e > 1.0) else max(1, int(np.ceil(np.log2(e / target) / order)))
-            if k + step > top:
-                if len(seen) >= 2 and seen[-2][1] > e > 0:  # fitted order from the last two runs
+            if k >= top:  # capped: extrapolate from the last two runs (their fitted order)
+                if len(seen) >= 2 and seen[-2][1] > e > 0:
                     (k0, e0, _), (k1, e1, s1) = seen[-2], seen[-1]
                     p = np.log2(e0 / e1) / (k1 - k0)
                     kx = k1 + int(np.ceil(np.log2(e1 / target) / p))
                     row.update(extrapolated=True, fitted_order=float(p), k=kx, dt=tf / 2 ** kx, steps=2 ** kx,
                                seconds=s1 * 2.0 ** (kx - k1), last_run={"k": k1, "error": e1, "seconds": s1})
                 break
-            k += step
+            k = min(k + step, top)
         out["methods"].append(row)
     return out
 
