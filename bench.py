@@ -213,7 +213,8 @@ def kind_name(k):
         parts.append(f"F{k['axis']}")
     if f & 4:
         parts.append(f"T I{k['axis']}")
-    name = {1: "axis_pass_pq_kernel", 2: "axis_pass_tma_kernel", 3: "axis_pass_tmap_kernel"}.get(
+    name = {1: "axis_pass_pq_kernel", 2: "axis_pass_tma_kernel", 3: "axis_pass_tmap_kernel",
+            4: "axis_pass_reg_kernel"}.get(
         k.get("variant"), "axis_pass_kernel")
     return "%s<L=%d,SV=%d%s> [%s]" % (name, N_GRID[k["axis"]], k["surfaces"], ",float2" if W["fp32"] else "",
                                       " ".join(parts))
@@ -223,7 +224,8 @@ def kind_name(k):
 # GPU arm
 # --------------------------------------------------------------------------
 
-KERNEL_SOURCES = ("axis_pass.cuh", "axis_pass_pq.cuh", "axis_pass_tma.cuh", "pass_args.h", "pass_launch.cuh")
+KERNEL_SOURCES = ("axis_pass.cuh", "axis_pass_pq.cuh", "axis_pass_reg.cuh", "axis_pass_tma.cuh", "pass_args.h",
+                  "pass_launch.cuh")
 
 
 def kernel_sources_hash() -> str:
@@ -422,7 +424,7 @@ def run_gpu(args):
                 "hbm_gbs_achieved": round(dom["bytes"] / (dom["avg_ms"] * 1e-3) / 1e9, 1),
                 "kinds": [{"kernel": kind_name(k), "avg_us": round(k["avg_ms"] * 1e3, 2),
                            "launches_per_step": k["launches_per_step"], "tile_lines": k["tile_lines"],
-                           "variant": ["tile", "persistent", "tma", "tma_persistent"][k["variant"]],
+                           "variant": ["tile", "persistent", "tma", "tma_persistent", "register"][k["variant"]],
                            "tflops": round(k["flops"] / (k["avg_ms"] * 1e-3) / 1e12, 4),
                            "gbs": round(k["bytes"] / (k["avg_ms"] * 1e-3) / 1e9, 1)} for k in kinds]})
     roofline["hbm_peak_gbs_measured"] = hbm_peak

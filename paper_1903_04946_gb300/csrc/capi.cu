@@ -35,6 +35,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/dso.h"
+#include "axis_pass_reg.cuh"
 #include "axis_pass_tma.cuh"
 #include "dso_internal.h"
 
@@ -610,12 +611,13 @@ dso_status autotune_tiles(dso_ctx* c) {
     int d, w, v, g, cp, used;
     while (sscanf(q, "%d,%d,%d,%d,%d;%n", &d, &w, &v, &g, &cp, &used) == 5) {
       q += used;
-      if (d < 0 || d >= c->Dv || w < 0 || w > 1 || v < 0 || v > 3 || g < 1 || (g & (g - 1))) continue;
+      if (d < 0 || d >= c->Dv || w < 0 || w > 1 || v < 0 || v > 4 || g < 1 || (g & (g - 1))) continue;
       if (c->vpart[d] == 1 && v != 0) continue;  // split-axis twiddles: tile kernel only
       const long long L = kind_L(c, d, w), lines = c->P / L;
       const int SV = w ? c->S : 1;
-      if (g > axis_pass_max_tile_lines((int)L, SV) || lines % g) continue;
-      if (c->prec == DSO_FP32 && v != 0) continue;
+      if (lines % g) continue;
+      if (v == 4 ? g != axis_pass_reg_lines((int)L, SV) : g > axis_pass_max_tile_lines((int)L, SV)) continue;
+      if (c->prec == DSO_FP32 && v != 0 && v != 4) continue;
       if ((v == 1 && !axis_pass_pq_supported((int)L, SV, g)) || (v == 2 && !axis_pass_tma_supported((int)L, SV, g)) ||
           (v == 3 && (!axis_pass_tmap_supported((int)L, SV, g) || c->Dv == 1)))
         continue;
@@ -684,14 +686,17 @@ dso_status autotune_tiles(dso_ctx* c) {
       int bestG = c->G[d][which], bestV = c->variant[d][which], bestC = c->cps[d][which];
       // DSO_VARIANT=v restricts the search to one kernel variant (testing)
       const char* fv = getenv("DSO_VARIANT");
-      const int only = (fv && fv[0] >= '0' && fv[0] <= '3') ? fv[0] - '0' : -1;
+      const int only = (fv && fv[0] >= '0' && fv[0] <= '4') ? fv[0] - '0' : -1;
       const bool both_tables = both[d][which];
-      for (int var = 0; var < 4 && err == cudaSuccess; ++var) {
+      const int greg = c->vpart[d] == 1 ? 0 : axis_pass_reg_lines(L, SV);
+      for (int var = 0; var < 5 && err == cudaSuccess; ++var) {
         if (only >= 0 && var != only) continue;
-        if (var != 0 && c->prec == DSO_FP32) continue;  // the other variants are FP64 only
+        if (var != 0 && var != 4 && c->prec == DSO_FP32) continue;  // variants 1-3 are FP64 only
         if (var == 3 && both_tables) continue;
-        for (long long G = 1; G <= gmax && G <= lines && err == cudaSuccess; G *= 2) {
-          if (any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
+        if (var == 4 && (greg == 0 || lines % greg)) continue;
+        for (long long G = var == 4 ? greg : 1; G <= (var == 4 ? greg : gmax) && G <= lines && err == cudaSuccess;
+             G *= 2) {
+          if (var != 4 && any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
           if (var == 1 && !axis_pass_pq_supported(L, SV, (int)G)) continue;
           if (var == 2 && !axis_pass_tma_supported(L, SV, (int)G)) continue;
           if (var == 3 && !axis_pass_tmap_supported(L, SV, (int)G)) continue;
@@ -2076,6 +2081,12 @@ bool axis_pass_tmap_supported(int L, int SV, int G) {
   const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
   const long long smem = 2LL * (SV + np) * G * L * 16 + (long long)L * 16 + 192;
   return SV * G * (L / 8) <= 256 && smem <= 220 * 1024 && encode_fn() != nullptr;
+}
+
+int axis_pass_reg_lines(int L, int SV) {
+  if (SV < 1 || SV > DSO_MAX_SURFACES || (L != 32 && L != 64 && L != 128)) return 0;
+  const int tpl = L == 32 ? RegPlan<32>::TPL : L == 64 ? RegPlan<64>::TPL : RegPlan<128>::TPL;
+  return (SV == 1 ? reg_threads<1>() : reg_threads<2>()) / tpl;
 }
 
 bool axis_pass_pq_supported(int L, int SV, int G) {

@@ -78,12 +78,16 @@ struct TmaMaps;
 // variant 2: one CTA per tile with TMA tile and table movement
 // (axis_pass_tma.cuh), which needs the tensor maps in `maps`; variant 3:
 // persistent CTAs with double-buffered TMA movement (axis_pass_tma.cuh),
-// which needs both `queue` and `maps`.
+// which needs both `queue` and `maps`; variant 4: lines of 32..128 points
+// held in registers (axis_pass_reg.cuh), axis_pass_reg_lines(L, SV) lines
+// per tile, where the amplitudes of the SV surfaces fit a thread's registers.
 cudaError_t launch_axis_pass(int L, int SV, int variant, const PassArgs& args, long long ntiles, unsigned* queue,
                              const TmaMaps* maps, cudaStream_t st);
 bool axis_pass_pq_supported(int L, int SV, int G);
 bool axis_pass_tma_supported(int L, int SV, int G);
 bool axis_pass_tmap_supported(int L, int SV, int G);
+// tile lines of the register-resident variant, 0 where it does not apply
+int axis_pass_reg_lines(int L, int SV);
 // per-SV launchers (one translation unit each)
 cudaError_t launch_axis_pass_sv1(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
                                  const TmaMaps* maps, cudaStream_t st);

@@ -5,6 +5,7 @@
 
 #include "axis_pass.cuh"
 #include "axis_pass_pq.cuh"
+#include "axis_pass_reg.cuh"
 #include "axis_pass_tma.cuh"
 #include "dso_internal.h"
 
@@ -140,9 +141,44 @@ cudaError_t launch_tmap(const PassArgs& a, const TmaMaps* maps, long long ntiles
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Register-resident variant (lines of 32..128 points): reg_lines<L, SV>() line
+// positions of SV surfaces per CTA, contiguous lines or lines of one outer row.
+template <int L, int SV, typename C>
+cudaError_t launch_reg_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
+  if constexpr (!reg_fits<L, SV, C>()) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const bool contig = a.stride_log2 == 0;
+    if (a.G != reg_lines<L, SV>() || (SV == 1 && (a.U1 || a.U2)) || (a.flags & PASS_XTW) ||
+        (!contig && a.stride_log2 < a.G_log2))
+      return cudaErrorInvalidConfiguration;
+    constexpr int NP = SV * (SV + 1) / 2;
+    const int np_staged = (SV > 1 && a.U1) ? (SV > 2 && a.dec0 ? NP - (SV - 1) : NP) : 0;
+    const size_t smem = reg_smem_bytes<L, SV>(contig, sizeof(C) == 8, np_staged);
+    const size_t smem_max = reg_smem_bytes<L, SV>(contig, sizeof(C) == 8, SV > 1 ? NP : 0);
+    if (smem_max > 227 * 1024) return cudaErrorInvalidConfiguration;
+    void (*k)(PassArgs) = contig ? axis_pass_reg_kernel<L, SV, true, C> : axis_pass_reg_kernel<L, SV, false, C>;
+    if (!attr_set[contig][dev]) {
+      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+      if (e != cudaSuccess) return e;
+      attr_set[contig][dev] = true;
+    }
+    const cudaError_t e = launch_k(k, (unsigned)ntiles, reg_threads<SV>(), smem, st, a.pdl != 0, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+}
+
 template <int L, int SV>
 cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, unsigned* queue, const TmaMaps* maps,
                            cudaStream_t st) {
+  if (variant == 4) {  // FP64 and FP32
+    if constexpr (L == 32 || L == 64 || L == 128)
+      return a.fp32 ? launch_reg_t<L, SV, float2>(a, ntiles, st) : launch_reg_t<L, SV, double2>(a, ntiles, st);
+    return cudaErrorInvalidConfiguration;
+  }
   if (variant != 0 && a.fp32) return cudaErrorInvalidConfiguration;  // FP64 only
   if (variant != 0 && (a.flags & PASS_XTW)) return cudaErrorInvalidConfiguration;  // split axes: tile kernel
   if (variant == 1) {

@@ -61,7 +61,7 @@ def test_batch_1d_many_jobs():
         assert_parity(out[b], oracle_propagate(jobs[b], 4, "triple_jump", 200.0, 1.0))
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
 def test_batch_all_variants(monkeypatch, variant):
     dso = require_gpu()
     monkeypatch.setenv("DSO_VARIANT", variant)

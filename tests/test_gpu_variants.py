@@ -3,7 +3,8 @@ autotuner normally picks the fastest; DSO_VARIANT forces one: 0 one CTA per
 tile with per-thread loads, 1 persistent CTAs with a tile queue and cp.async
 prefetch, 2 TMA bulk tensor copies (lines up to 256 points), 3 persistent
 CTAs with TMA copies double-buffered against the FFT work (lines up to 256
-points; 1-D grids fall back to another variant)."""
+points; 1-D grids fall back to another variant), 4 lines of 32..128 points
+of the one-surface passes held in registers (the other kinds fall back)."""
 import numpy as np
 import pytest
 
@@ -22,7 +23,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_variant_parity(monkeypatch, variant, case):
     require_gpu()
@@ -38,7 +39,7 @@ def test_variants_agree_bitwise_or_closely(monkeypatch):
     require_gpu()
     pr = synth.pyrazine_like(seed=8, n=(32, 32, 32))
     outs = []
-    for v in ("0", "1", "2", "3"):
+    for v in ("0", "1", "2", "3", "4"):
         monkeypatch.setenv("DSO_VARIANT", v)
         outs.append(gpu_propagate(pr, 4, "suzuki", 50.0, 25.0))
     for o in outs[1:]:
@@ -46,7 +47,7 @@ def test_variants_agree_bitwise_or_closely(monkeypatch):
         assert np.array_equal(o, outs[0])
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
 @pytest.mark.parametrize("n,S", [((16, 32, 8), 3), ((256,), 2)])
 def test_variant_parity_tvt(monkeypatch, variant, n, S):
     require_gpu()
@@ -94,7 +95,7 @@ def test_programmatic_dependent_launch_changes_nothing(monkeypatch):
     outs = []
     for flag in ("1", "0"):
         monkeypatch.setenv("DSO_PDL", flag)
-        for v in ("0", "2", "3"):
+        for v in ("0", "2", "3", "4"):
             monkeypatch.setenv("DSO_VARIANT", v)
             outs.append(gpu_propagate(pr, 6, "suzuki", 3 * 25.0, 25.0))
     for o in outs[1:]:
