@@ -183,7 +183,8 @@ def pass_flops_bytes(kind, n, S, esz=16):
     5 L log2 L flops per complex FFT of a length-L line, 8 S^2 - 2 S flops per
     grid point per S x S complex matvec, 6 flops per amplitude for the kinetic
     phase; bytes = psi read + write (16 B per amplitude each) plus the
-    operator tables read (16 B per packed complex entry)."""
+    operator tables read (16 B per packed complex entry; a separable kinetic
+    phase table has only L entries)."""
     import math
     P = 1
     for x in n:
@@ -196,9 +197,9 @@ def pass_flops_bytes(kind, n, S, esz=16):
     nU = (1 if f & 256 else 0) + (1 if f & 512 else 0)
     flops += nU * (8 * S * S - 2 * S) * P
     bytes_ = 2 * esz * amps + nU * esz * (S * (S + 1) // 2) * P
-    if f & 4:
+    if f & 4:  # the kinetic phase: a grid-sized table, or (flag 16) one of this axis alone
         flops += 6 * amps
-        bytes_ += esz * P
+        bytes_ += esz * (L if f & 16 else P)
     return flops, bytes_
 
 
@@ -212,7 +213,7 @@ def kind_name(k):
     if f & 2:
         parts.append(f"F{k['axis']}")
     if f & 4:
-        parts.append(f"T I{k['axis']}")
+        parts.append(f"T{k['axis']} I{k['axis']}" if f & 16 else f"T I{k['axis']}")
     name = {1: "axis_pass_pq_kernel", 2: "axis_pass_tma_kernel", 3: "axis_pass_tmap_kernel",
             4: "axis_pass_reg_kernel"}.get(
         k.get("variant"), "axis_pass_kernel")
@@ -292,6 +293,8 @@ def run_gpu(args):
     ctx = dso.Context(device=device, stream=stream, precision=dso.DSO_FP32 if fp32 else dso.DSO_FP64)
     ctx.load_problem(pr)
     dso.dso_set_scheme(ctx.ctx, ORDER, scheme_code())
+    kin_mode = {"joint": dso.DSO_KINETIC_JOINT, "axes": dso.DSO_KINETIC_AXES}[args.kinetic]
+    dso.dso_set_kinetic_mode(ctx.ctx, kin_mode)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
 
     def barrier():
@@ -493,7 +496,8 @@ def run_gpu(args):
                 "data": "synthetic (seeded)",
                 "config": config_dict({"l2": "flushed before every timed step (256 MiB write outside the "
                                              "per-step CUDA events)",
-                                       "substeps_per_step": nsub, "grid_points": pts}),
+                                       "substeps_per_step": nsub, "grid_points": pts,
+                                       "kinetic_step": "per axis" if args.kinetic == "axes" else "joint"}),
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
                 "graph_replay": graph}
         if cpu is not None:
@@ -524,8 +528,10 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
     jump order 4: device-timed steps (L2 flushed before each), the step's
     roofline counted with algorithmic bytes -- psi read and written once per
     fused pass pair (32 B per amplitude-substep in FP32) plus the operator
-    tables read (the loaded potential entries and the kinetic phase, 8 B
-    each per grid point) -- and the error against the FP64 path."""
+    tables read per grid point (the loaded potential entries and, for the
+    joint kinetic step, its phase, 8 B each) -- and the error against the
+    FP64 path.  The value is the library's default form of the kinetic step
+    (joint); the per-axis form (DSO_KINETIC_AXES) is timed beside it."""
     import numpy as np
     import torch
 
@@ -537,29 +543,38 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
     a, b, *_ = dso.dso_scheme_coefficients(order, dso.DSO_TRIPLE_JUMP)
     nsub = len(b)
     stream = torch.cuda.Stream(device=device)
-    ctx = dso.Context(device=device, stream=stream, precision=dso.DSO_FP32)
-    ctx.load_problem(pr)
-    dso.dso_set_scheme(ctx.ctx, order, dso.DSO_TRIPLE_JUMP)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
-    for _ in range(warmup):
-        ctx.propagate(dt, dt)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for k in range(steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            ctx.propagate(dt, dt)
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
-    ctx.close()
-    # surface 0 is uncoupled in this model: the potential step reads 4 of the
-    # 6 packed entries (S(S+1)/2 - (S-1)); plus one kinetic phase per point
-    tab_entries = S_ * (S_ + 1) // 2 - (S_ - 1) + 1
-    bytes_step = nsub * (32 * S_ * pts + 8 * tab_entries * pts)
     peak, src = _hbm_peak()
-    gbs = bytes_step / (ms * 1e-3) / 1e9
+
+    def timed(mode):
+        ctx = dso.Context(device=device, stream=stream, precision=dso.DSO_FP32)
+        ctx.load_problem(pr)
+        dso.dso_set_scheme(ctx.ctx, order, dso.DSO_TRIPLE_JUMP)
+        dso.dso_set_kinetic_mode(ctx.ctx, mode)
+        for _ in range(warmup):
+            ctx.propagate(dt, dt)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                ctx.propagate(dt, dt)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+        plan = dso.dso_tuned_plan(ctx.ctx)
+        ctx.close()
+        # surface 0 is uncoupled in this model: the potential step reads 4 of
+        # the 6 packed entries (S(S+1)/2 - (S-1)); the joint kinetic step one
+        # phase per point (the per-axis tables hold sum_d n_d entries)
+        tab_entries = S_ * (S_ + 1) // 2 - (S_ - 1) + (1 if mode == dso.DSO_KINETIC_JOINT else 0)
+        bytes_step = nsub * (32 * S_ * pts + 8 * tab_entries * pts)
+        gbs = bytes_step / (ms * 1e-3) / 1e9
+        return ms, bytes_step, gbs, plan
+
+    ms, bytes_step, gbs, plan = timed(dso.DSO_KINETIC_JOINT)
+    ms_x, bytes_x, gbs_x, _ = timed(dso.DSO_KINETIC_AXES)
     c32 = dso.Context(pr, device=device, order=order, scheme=dso.DSO_TRIPLE_JUMP, precision=dso.DSO_FP32)
     c64 = dso.Context(pr, device=device, order=order, scheme=dso.DSO_TRIPLE_JUMP, precision=dso.DSO_FP64)
     c32.propagate(check_steps * dt, dt)
@@ -573,11 +588,16 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
                         "(FP64 angles, coefficients and reductions), triple jump order 4, dt = 2000/128 a.u.",
             "value": pts * nsub / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "substeps_per_step": nsub, "l2": "flushed before every timed step",
+            "kinetic_step": "joint (phase of the whole grid between full transforms)", "plan": plan,
             "roofline": {"bound": "hbm", "bytes_per_step": bytes_step, "achieved": round(gbs, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
                          "bytes": "algorithmic: 32 B per amplitude-substep (psi read + written by two fused "
                                   "passes) + 8 B per grid point per table entry read (4 potential entries, "
                                   "1 kinetic phase)"},
+            "per_axis_kinetic_step": {"ms_per_step": ms_x, "value": pts * nsub / (ms_x * 1e-3),
+                                      "roofline_frac": round(gbs_x / peak, 4),
+                                      "bytes": "as above without the kinetic phase (per-axis tables of "
+                                               "sum_d n_d entries)"},
             "error_vs_fp64": {"steps": check_steps, "rel_l2": err, "norm_drift": float(abs(n32 - 1.0)),
                               "reference": "FP64 GPU path, same input and steps"}}
 
@@ -823,6 +843,8 @@ def main():
                     help="skip the sub-records (FP32 precision mode, time to 1e-10, serving)")
     ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
     ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
+    ap.add_argument("--kinetic", default="joint", choices=["joint", "axes"],
+                    help="form of the kinetic step (dso_set_kinetic_mode)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="after the warm-up, run this many steps inside cudaProfilerStart/Stop and exit "
                          "(for ncu --profile-from-start off)")

@@ -22,6 +22,7 @@ DSO_FP64, DSO_FP32 = 0, 1
 DSO_TRIPLE_JUMP, DSO_SUZUKI, DSO_OPTIMAL = 0, 1, 2
 SCHEME_CODES = {"triple_jump": DSO_TRIPLE_JUMP, "suzuki": DSO_SUZUKI, "optimal": DSO_OPTIMAL}
 DSO_VTV, DSO_TVT, DSO_VT, DSO_TV = 0, 1, 2, 3
+DSO_KINETIC_JOINT, DSO_KINETIC_AXES = 0, 1
 
 EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
@@ -32,6 +33,7 @@ EXPORTS = (
     "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer", "dso_set_pass_limits",
     "dso_batch_create", "dso_batch_destroy", "dso_batch_add", "dso_batch_step", "dso_batch_sync",
     "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count", "dso_batch_busy",
+    "dso_set_kinetic_mode",
 )
 
 _lib = None
@@ -82,6 +84,7 @@ def load(path: str = LIB):
         "dso_set_wait_probe": (i32, [vp, i32]),
         "dso_psi_device_pointer": (i32, [vp, ctypes.POINTER(vp)]),
         "dso_set_pass_limits": (i32, [vp, i32, i32]),
+        "dso_set_kinetic_mode": (i32, [vp, i32]),
         "dso_batch_create": (i32, [ctypes.POINTER(vp), i32, i32, vp]),
         "dso_batch_destroy": (None, [vp]),
         "dso_batch_add": (i32, [vp, vp, dbl, dbl, ctypes.POINTER(i32)]),
@@ -316,6 +319,10 @@ def device_view(ptr: int, shape, dtype, device=0):
 
 def dso_set_pass_limits(ctx, max_line, max_tile):
     _check(load().dso_set_pass_limits(ctx, int(max_line), int(max_tile)), "dso_set_pass_limits")
+
+
+def dso_set_kinetic_mode(ctx, mode):
+    _check(load().dso_set_kinetic_mode(ctx, int(mode)), "dso_set_kinetic_mode")
 
 
 def dso_batch_create(device: int = 0, precision: int = DSO_FP64, stream=None):

@@ -524,12 +524,30 @@ __device__ __forceinline__ void apply_potential(C* sm, const C* __restrict__ U, 
 
 // `scale` multiplies the phase (1 for the first kinetic table; P for a second
 // one, whose 1/P factor belongs to an inverse FFT that does not run twice).
+// With `axis_table` the phase is this axis's alone: element n of every line
+// takes tau[n] (separable kinetic step).
 template <int L, typename C>
 __device__ __forceinline__ void apply_kinetic(C* sm, const C* __restrict__ tau, const TileGeom& tg, int G, int SVl,
                                               long long stride, int tid, int nthr, RealT<C> scale,
-                                              const SmemLayout lay, const PassArgs* dbg = nullptr) {
+                                              const SmemLayout lay, const PassArgs* dbg = nullptr,
+                                              bool axis_table = false) {
   const int tile_pts = G * L;
   const int tile_sz = G * lay.ls;
+  if (axis_table) {
+    for (int e = tid; e < tile_pts; e += nthr) {
+      int g, n;
+      tile_elem<L>(e, tg, g, n);
+      C t = __ldg(&tau[n]);
+      if (scale != (RealT<C>)1) t = cscale(t, scale);
+      const int off = g * lay.ls + lay.pos(n);
+      for (int s = 0; s < SVl; ++s) {
+        C* p = &sm[(size_t)s * tile_sz + off];
+        *p = cmul(*p, t);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if (tg.stride_log2 == 0) {  // contiguous lines: the tile's phases are one block
     const C* blk = tau + (size_t)tg.o0 * L;
     for (int e = tid; e < tile_pts; e += nthr) {
@@ -691,10 +709,12 @@ __global__ void __launch_bounds__(MaxThreads<L, SV>::value) axis_pass_kernel(Pas
   }
   if (a.flags & PASS_T) {
     __syncthreads();
-    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr, (RealT<C>)1, lay, &a);
+    const bool tax = (a.flags & PASS_TAX) != 0;
+    apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau), tg, G, SV, a.stride, tid, nthr, (RealT<C>)1, lay, &a,
+                     tax);
     if (a.tau2)
       apply_kinetic<L>(sm, reinterpret_cast<const C*>(a.tau2), tg, G, SV, a.stride, tid, nthr,
-                       (RealT<C>)a.tau2_scale, lay, &a);
+                       (RealT<C>)a.tau2_scale, lay, &a, tax);
     fft_lines<L, true, K>(sm, tw, nslots, tid, nthr, lay);
   }
   __syncthreads();

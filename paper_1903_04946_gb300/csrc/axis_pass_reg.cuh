@@ -47,12 +47,12 @@ struct RegPlan<128> {
   static constexpr int TPL = 8, VPT = 16;
 };
 
-// Threads per CTA: 256 for one staged surface; 128 for S surfaces, whose
-// amplitudes take most of a thread's registers, so that two CTAs share an
-// SM and one's loads overlap the other's FFTs.
+// Threads per CTA: 128, four CTAs per SM for one staged surface and two for
+// S surfaces (whose amplitudes take most of a thread's registers), so that
+// one CTA's loads overlap another's FFTs and a pass's last CTAs are short.
 template <int SV>
 __host__ __device__ constexpr int reg_threads() {
-  return SV == 1 ? 256 : 128;
+  return 128;
 }
 
 // Line positions per CTA (the tile line count G the host must use).
@@ -62,62 +62,147 @@ __host__ __device__ constexpr int reg_lines() {
 }
 
 // Exchange buffer of one line: element n at n + (n >> plog), lines LS apart.
-template <int L, bool CONTIG>
+template <int L, bool WL>
 struct RegLayout {
-  static constexpr int plog = CONTIG ? (L == 128 ? 4 : 3) : 31;
-  static constexpr int LS = CONTIG ? L + (L >> plog) : L + 1;
+  static constexpr int plog = WL ? (L == 128 ? 4 : 3) : 31;
+  static constexpr int LS = WL ? L + (L >> plog) : L + 1;
   __device__ __forceinline__ static int pos(int n) { return plog < 31 ? n + (n >> plog) : n; }
 };
 
-template <bool CONTIG>
+template <bool WL>
 __device__ __forceinline__ void reg_sync() {
-  if (CONTIG) __syncwarp(); else __syncthreads();
+  if (WL) __syncwarp(); else __syncthreads();
+}
+
+// The butterflies of axis_pass.cuh with the transform's direction as a
+// runtime sign sg = +1 (forward, exp(-i ..)) or -1 (inverse): every INV
+// branch there becomes a multiplication by sg, which is exact, so each
+// output is the template version's, bit for bit.  One body serves both
+// directions, halving the kernel's straight-line code.
+template <typename C>
+__device__ __forceinline__ C rot_i_s(C a, RealT<C> sg) {  // -i a (forward), +i a (inverse)
+  return mkc(sg * a.y, -sg * a.x);
+}
+
+template <typename C>
+__device__ __forceinline__ void dft4_s(C& a0, C& a1, C& a2, C& a3, RealT<C> sg) {
+  C t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  C t2 = cadd(a1, a3), t3 = rot_i_s(csub(a1, a3), sg);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <typename C>
+__device__ __forceinline__ void dft8_s(C* x, RealT<C> sg) {
+  using R = RealT<C>;
+  const R c = (R)0.70710678118654752440;  // 1/sqrt(2)
+  C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4_s(e0, e1, e2, e3, sg);
+  dft4_s(o0, o1, o2, o3, sg);
+  x[0] = cadd(e0, o0);
+  x[4] = csub(e0, o0);
+  C r2 = rot_i_s(o2, sg);
+  x[2] = cadd(e2, r2);
+  x[6] = csub(e2, r2);
+  // forward (x + y, y - x), inverse (x - y, x + y)
+  C u1 = mkc(o1.x + sg * o1.y, o1.y - sg * o1.x);
+  x[1] = mkc(fma(c, u1.x, e1.x), fma(c, u1.y, e1.y));
+  x[5] = mkc(fma(-c, u1.x, e1.x), fma(-c, u1.y, e1.y));
+  // forward (y - x, -(x + y)), inverse (-(x + y), x - y)
+  C u3 = mkc(sg * o3.y - o3.x, -sg * o3.x - o3.y);
+  x[3] = mkc(fma(c, u3.x, e3.x), fma(c, u3.y, e3.y));
+  x[7] = mkc(fma(-c, u3.x, e3.x), fma(-c, u3.y, e3.y));
+}
+
+// tan_pair with the twiddle's tangent already signed (ts = sg t) and, for
+// the rotated pairs, its cosine signed (cs = sg c).
+template <bool ROT, typename C>
+__device__ __forceinline__ void tan_pair_s(C& a, C& b, RealT<C> c, RealT<C> ts, RealT<C> cs) {
+  const auto zx = fma(-ts, b.y, b.x);
+  const auto zy = fma(ts, b.x, b.y);
+  C p, q;
+  if (!ROT) {
+    p = mkc(fma(c, zx, a.x), fma(c, zy, a.y));
+    q = mkc(fma(-c, zx, a.x), fma(-c, zy, a.y));
+  } else {
+    p = mkc(fma(cs, zy, a.x), fma(-cs, zx, a.y));
+    q = mkc(fma(-cs, zy, a.x), fma(cs, zx, a.y));
+  }
+  a = p;
+  b = q;
+}
+
+template <typename C>
+__device__ __forceinline__ void dft8_tw_s(C* x, C w1, C w2, C w4, C w8, RealT<C> sg) {
+  const auto t1 = sg * w1.y, t2 = sg * w2.y, t4 = sg * w4.y, t8 = sg * w8.y;
+  const auto c1 = sg * w1.x, c2 = sg * w2.x, c8 = sg * w8.x;
+  tan_pair_s<false>(x[0], x[4], w4.x, t4, t4);
+  tan_pair_s<false>(x[2], x[6], w4.x, t4, t4);
+  tan_pair_s<false>(x[1], x[5], w4.x, t4, t4);
+  tan_pair_s<false>(x[3], x[7], w4.x, t4, t4);
+  tan_pair_s<false>(x[0], x[2], w2.x, t2, c2);
+  tan_pair_s<true>(x[4], x[6], w2.x, t2, c2);
+  tan_pair_s<false>(x[1], x[3], w2.x, t2, c2);
+  tan_pair_s<true>(x[5], x[7], w2.x, t2, c2);
+  tan_pair_s<false>(x[0], x[1], w1.x, t1, c1);
+  tan_pair_s<false>(x[4], x[5], w8.x, t8, c8);
+  tan_pair_s<true>(x[2], x[3], w1.x, t1, c1);
+  tan_pair_s<true>(x[6], x[7], w8.x, t8, c8);
+  const C y1 = x[4], y4 = x[1], y3 = x[6], y6 = x[3];
+  x[1] = y1;
+  x[4] = y4;
+  x[3] = y3;
+  x[6] = y6;
 }
 
 // Inverse or forward FFT of SV lines (one per staged surface) at this
 // thread's line position.  The register stages of all SV lines share the
 // twiddle loads; the lines go through the one exchange buffer (G lines) in
 // turn.
-template <int L, int SV, bool INV, bool CONTIG, typename C>
-__device__ __forceinline__ void fft_reg(C (&v)[SV][RegPlan<L>::VPT], C* ln, int t, const C* __restrict__ tw) {
-  using LY = RegLayout<L, CONTIG>;
+template <int L, int SV, bool WL, typename C>
+__device__ __forceinline__ void fft_reg(C (&v)[SV][RegPlan<L>::VPT], C* ln, int t, const C* __restrict__ tw,
+                                        RealT<C> sg) {
+  using LY = RegLayout<L, WL>;
   C w1, w2, w4, w8;
   if constexpr (L == 64) {
 #pragma unroll
-    for (int s = 0; s < SV; ++s) dftR<8, INV>(v[s]);  // stage 1 (Ls = 1): j = t on x[t + 8r]; y[8t + r]
+    for (int s = 0; s < SV; ++s) dft8_s(v[s], sg);  // stage 1 (Ls = 1): j = t on x[t + 8r]; y[8t + r]
 #pragma unroll
     for (int s = 0; s < SV; ++s) {
-      reg_sync<CONTIG>();  // earlier readers of the buffer are done
+      reg_sync<WL>();  // earlier readers of the buffer are done
 #pragma unroll
       for (int r = 0; r < 8; ++r) ln[LY::pos(8 * t + r)] = v[s][r];
-      reg_sync<CONTIG>();
+      reg_sync<WL>();
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[s][r] = ln[LY::pos(t + 8 * r)];
     }
     load_tw8<64>(tw, t, w1, w2, w4, w8);  // stage 2 (Ls = 8): butterfly k = t
 #pragma unroll
-    for (int s = 0; s < SV; ++s) dft8_tw<INV>(v[s], w1, w2, w4, w8);  // X[t + 8r] = v[r]
+    for (int s = 0; s < SV; ++s) dft8_tw_s(v[s], w1, w2, w4, w8, sg);  // X[t + 8r] = v[r]
   } else if constexpr (L == 128) {
 #pragma unroll
     for (int s = 0; s < SV; ++s) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) dft2<INV>(v[s][r], v[s][r + 8]);  // stage 1: j = t + 8r -> y[2j], y[2j + 1]
+      for (int r = 0; r < 8; ++r) dft2<false>(v[s][r], v[s][r + 8]);  // stage 1: j = t + 8r -> y[2j], y[2j + 1]
     }
     load_tw8<128>(tw, 0, w1, w2, w4, w8);  // stage 2 (Ls = 2): j = 2t (k = 0), inputs y[2t + 16r]
 #pragma unroll
-    for (int s = 0; s < SV; ++s) dft8_tw<INV>(&v[s][0], w1, w2, w4, w8);
+    for (int s = 0; s < SV; ++s) dft8_tw_s(&v[s][0], w1, w2, w4, w8, sg);
     load_tw8<128>(tw, 8, w1, w2, w4, w8);  // j = 2t + 1 (k = 1), inputs y[2t + 1 + 16r]
 #pragma unroll
-    for (int s = 0; s < SV; ++s) dft8_tw<INV>(&v[s][8], w1, w2, w4, w8);
+    for (int s = 0; s < SV; ++s) dft8_tw_s(&v[s][8], w1, w2, w4, w8, sg);
 #pragma unroll
     for (int s = 0; s < SV; ++s) {
-      reg_sync<CONTIG>();
+      reg_sync<WL>();
 #pragma unroll
       for (int r = 0; r < 8; ++r) {  // z[16t + 2r] from j = 2t, z[16t + 2r + 1] from j = 2t + 1
         ln[LY::pos(16 * t + 2 * r)] = v[s][r];
         ln[LY::pos(16 * t + 2 * r + 1)] = v[s][8 + r];
       }
-      reg_sync<CONTIG>();
+      reg_sync<WL>();
 #pragma unroll
       for (int r = 0; r < 8; ++r) {  // z[t + 16r], z[t + 8 + 16r]: the elements t + 8m, m = 2r, 2r + 1
         v[s][2 * r] = ln[LY::pos(t + 16 * r)];
@@ -130,7 +215,7 @@ __device__ __forceinline__ void fft_reg(C (&v)[SV][RegPlan<L>::VPT], C* ln, int 
       C a[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) a[r] = v[s][2 * r];
-      dft8_tw<INV>(a, w1, w2, w4, w8);  // X[t + 16r]
+      dft8_tw_s(a, w1, w2, w4, w8, sg);  // X[t + 16r]
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[s][2 * r] = a[r];
     }
@@ -140,31 +225,31 @@ __device__ __forceinline__ void fft_reg(C (&v)[SV][RegPlan<L>::VPT], C* ln, int 
       C b[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) b[r] = v[s][2 * r + 1];
-      dft8_tw<INV>(b, w1, w2, w4, w8);  // X[t + 8 + 16r]
+      dft8_tw_s(b, w1, w2, w4, w8, sg);  // X[t + 8 + 16r]
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[s][2 * r + 1] = b[r];
     }
   } else {  // L == 32
 #pragma unroll
     for (int s = 0; s < SV; ++s) {
-      dft4<INV>(v[s][0], v[s][2], v[s][4], v[s][6]);  // stage 1: j = t on x[t + 8r]; y[4t + r]
-      dft4<INV>(v[s][1], v[s][3], v[s][5], v[s][7]);  // j = t + 4 on x[t + 4 + 8r]; y[4t + 16 + r]
+      dft4_s(v[s][0], v[s][2], v[s][4], v[s][6], sg);  // stage 1: j = t on x[t + 8r]; y[4t + r]
+      dft4_s(v[s][1], v[s][3], v[s][5], v[s][7], sg);  // j = t + 4 on x[t + 4 + 8r]; y[4t + 16 + r]
     }
 #pragma unroll
     for (int s = 0; s < SV; ++s) {
-      reg_sync<CONTIG>();
+      reg_sync<WL>();
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         ln[LY::pos(4 * t + r)] = v[s][2 * r];
         ln[LY::pos(4 * t + 16 + r)] = v[s][2 * r + 1];
       }
-      reg_sync<CONTIG>();
+      reg_sync<WL>();
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[s][r] = ln[LY::pos(t + 4 * r)];
     }
     load_tw8<32>(tw, t, w1, w2, w4, w8);  // stage 2 (Ls = 4): butterfly k = t
 #pragma unroll
-    for (int s = 0; s < SV; ++s) dft8_tw<INV>(v[s], w1, w2, w4, w8);  // X[t + 4r] = v[r]
+    for (int s = 0; s < SV; ++s) dft8_tw_s(v[s], w1, w2, w4, w8, sg);  // X[t + 4r] = v[r]
   }
 }
 
@@ -253,16 +338,20 @@ __host__ __device__ constexpr bool reg_fits() {
 // propagation, so their copies are issued before the wait for the previous
 // pass and land while this tile's wavefunction loads and inverse FFT run.
 template <int L, int SV, bool CONTIG, typename C>
-__global__ void __launch_bounds__(reg_threads<SV>(), 2) axis_pass_reg_kernel(PassArgs a) {
+__global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_reg_kernel(PassArgs a) {
   constexpr int TPL = RegPlan<L>::TPL, VPT = RegPlan<L>::VPT, G = reg_lines<L, SV>(), NT = reg_threads<SV>();
-  using LY = RegLayout<L, CONTIG>;
+  constexpr bool WL = CONTIG;  // a line's threads in one warp (contiguous lines)
+  using LY = RegLayout<L, WL>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int tid = threadIdx.x;
-  // contiguous lines: a line's TPL threads are consecutive lanes; strided
-  // lines: consecutive lanes take consecutive lines (coalesced)
-  const int g = CONTIG ? tid / TPL : tid % G;
-  const int t = CONTIG ? tid % TPL : tid / G;
+  // contiguous lines: a line's TPL threads are consecutive lanes (a warp
+  // barrier in the exchange); strided lines: consecutive lanes take
+  // consecutive lines (coalesced; a block barrier).  A mapping of strided
+  // lines with a line's threads in one warp (rows of 32 bytes per access)
+  // measured 1.45x slower on 128-point FP32 lines.
+  const int g = WL ? tid / TPL : tid % G;
+  const int t = WL ? tid % TPL : tid / G;
   const TileJob tj = split_tile(blockIdx.x, SV, a);
   const TileGeom tg = make_geom(tj.tile, a);
   // Element m of this thread's part of the line sits at line + off(m); the
@@ -291,35 +380,55 @@ __global__ void __launch_bounds__(reg_threads<SV>(), 2) axis_pass_reg_kernel(Pas
     for (int m = 0; m < VPT; ++m) v[s][m] = psi[(size_t)s * a.P + ((unsigned)(t + TPL * m) << sh)];
   }
   pdl_trigger();
-  if (a.flags & PASS_INV_FIRST) fft_reg<L, SV, true, CONTIG>(v, ln, t, tw);
-  if (SV > 1 && a.U1) {
-    const unsigned after = potential_reg<L, SV, NT>(v, us, a.dec0, tid);
-    if (a.U2) {  // the second table goes through the same slots of this thread, copied once they are read
-      stage_potential<L, SV, NT>(us + after, reinterpret_cast<const C*>(a.U2) + uoff, a.P, t, sh, a.dec0, tid);
-      potential_reg<L, SV, NT>(v, us, a.dec0, tid);
-    }
+  // The pass's steps in order: inverse FFT, potential step(s), forward FFT,
+  // kinetic phase(s), inverse FFT.  With several surfaces they run as one
+  // loop whose body holds one FFT (the sign a runtime value), so that the
+  // straight-line code -- run once per tile -- stays small: unrolled, the
+  // three-surface body's instruction fetches stalled its warps as often as
+  // its memory loads did.  One surface keeps the unrolled sequence (fewer
+  // registers).
+  const int f = a.flags;
+  const bool pot = SV > 1 && a.U1;
+  constexpr int J0 = SV == 1 ? 1 : 0;  // step 0 of the one-surface sequence is unrolled below
+  if constexpr (SV == 1) {
+    if (f & PASS_INV_FIRST) fft_reg<L, SV, WL>(v, ln, t, tw, (RealT<C>)-1);
+    if (f & PASS_FWD) fft_reg<L, SV, WL>(v, ln, t, tw, (RealT<C>)1);
   }
-  if (a.flags & PASS_FWD) {
-    fft_reg<L, SV, false, CONTIG>(v, ln, t, tw);
-    if (a.flags & PASS_T) {  // the kinetic phase(s), as apply_kinetic, then the inverse FFT
-      const C* tau = reinterpret_cast<const C*>(a.tau) + line;
+#pragma unroll(SV == 1 ? 4 : 1)
+  for (int j = J0; j < 5; ++j) {
+    if (SV == 1 && j == 2) continue;  // the forward FFT ran above
+    const bool fft = (j == 0 && (f & PASS_INV_FIRST)) || (j == 2 && (f & PASS_FWD)) ||
+                     (j == 4 && (f & PASS_FWD) && (f & PASS_T));
+    if (fft) {
+      fft_reg<L, SV, WL>(v, ln, t, tw, j == 2 ? (RealT<C>)1 : (RealT<C>)-1);
+    } else if (j == 1 && pot) {
+      const unsigned after = potential_reg<L, SV, NT>(v, us, a.dec0, tid);
+      if (a.U2) {  // the second table goes through the same slots of this thread, copied once they are read
+        stage_potential<L, SV, NT>(us + after, reinterpret_cast<const C*>(a.U2) + uoff, a.P, t, sh, a.dec0, tid);
+        potential_reg<L, SV, NT>(v, us, a.dec0, tid);
+      }
+    } else if (j == 3 && (f & PASS_FWD) && (f & PASS_T)) {  // the kinetic phase(s), as apply_kinetic
+      // a table of the grid (element at line + off(m)) or of this axis alone (element t + TPL m)
+      const bool tax = (f & PASS_TAX) != 0;
+      const long long tline = tax ? 0 : line;
+      const int tsh = tax ? 0 : sh;
+      const C* tau = reinterpret_cast<const C*>(a.tau) + tline;
 #pragma unroll
       for (int m = 0; m < VPT; ++m) {
-        const C ph = __ldg(&tau[(unsigned)(t + TPL * m) << sh]);
+        const C ph = __ldg(&tau[(unsigned)(t + TPL * m) << tsh]);
 #pragma unroll
         for (int s = 0; s < SV; ++s) v[s][m] = cmul(v[s][m], ph);
       }
       if (a.tau2) {
-        const C* tau2 = reinterpret_cast<const C*>(a.tau2) + line;
+        const C* tau2 = reinterpret_cast<const C*>(a.tau2) + tline;
 #pragma unroll
         for (int m = 0; m < VPT; ++m) {
-          C ph = __ldg(&tau2[(unsigned)(t + TPL * m) << sh]);
+          C ph = __ldg(&tau2[(unsigned)(t + TPL * m) << tsh]);
           if ((RealT<C>)a.tau2_scale != (RealT<C>)1) ph = cscale(ph, (RealT<C>)a.tau2_scale);
 #pragma unroll
           for (int s = 0; s < SV; ++s) v[s][m] = cmul(v[s][m], ph);
         }
       }
-      fft_reg<L, SV, true, CONTIG>(v, ln, t, tw);
     }
   }
   // With several surfaces the store addresses are recomputed from an opaque
@@ -337,8 +446,8 @@ __global__ void __launch_bounds__(reg_threads<SV>(), 2) axis_pass_reg_kernel(Pas
 // Shared memory of a tile: the exchange buffer and, with a potential step,
 // the staging buffer of the np_staged packed entries the pass loads.
 template <int L, int SV>
-inline size_t reg_smem_bytes(bool contig, bool fp32, int np_staged) {
-  const int LS = contig ? RegLayout<L, true>::LS : RegLayout<L, false>::LS;
+inline size_t reg_smem_bytes(bool wl, bool fp32, int np_staged) {
+  const int LS = wl ? RegLayout<L, true>::LS : RegLayout<L, false>::LS;
   const size_t esz = fp32 ? 8 : 16;
   return ((size_t)reg_lines<L, SV>() * LS + (size_t)np_staged * RegPlan<L>::VPT * reg_threads<SV>()) * esz;
 }

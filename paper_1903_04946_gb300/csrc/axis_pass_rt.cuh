@@ -155,9 +155,24 @@ __device__ __forceinline__ void potential_rt_sv(int SV, C* sm, const C* U, const
 template <typename C>
 __device__ __forceinline__ void kinetic_rt(C* sm, const C* __restrict__ tau, const TileGeom& tg, int G, int L,
                                            int log2L, int SVl, long long stride, int tid, int nthr, RealT<C> scale,
-                                           const SmemLayout lay) {
+                                           const SmemLayout lay, bool axis_table) {
   const int tile_pts = G * L;
   const int tile_sz = G * lay.ls;
+  if (axis_table) {  // the phase of this axis alone: element n of every line takes tau[n]
+    for (int e = tid; e < tile_pts; e += nthr) {
+      int g, n;
+      tile_elem_rt(e, tg, L, log2L, g, n);
+      C t = __ldg(&tau[n]);
+      if (scale != (RealT<C>)1) t = cscale(t, scale);
+      const int off = g * lay.ls + lay.pos(n);
+      for (int s = 0; s < SVl; ++s) {
+        C* p = &sm[(size_t)s * tile_sz + off];
+        *p = cmul(*p, t);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if (tg.stride_log2 == 0) {  // contiguous lines: the tile's phases are one block
     const C* blk = tau + (size_t)tg.o0 * L;
     for (int e = tid; e < tile_pts; e += nthr) {
@@ -277,10 +292,12 @@ __device__ __forceinline__ void tile_pass_rt(C* sm, const PassArgs& a, int L, in
   }
   if (a.flags & PASS_T) {
     __syncthreads();
-    kinetic_rt(sm, reinterpret_cast<const C*>(a.tau), tg, G, L, log2L, SV, a.stride, tid, nthr, (RealT<C>)1, lay);
+    const bool tax = (a.flags & PASS_TAX) != 0;
+    kinetic_rt(sm, reinterpret_cast<const C*>(a.tau), tg, G, L, log2L, SV, a.stride, tid, nthr, (RealT<C>)1, lay,
+               tax);
     if (a.tau2)
       kinetic_rt(sm, reinterpret_cast<const C*>(a.tau2), tg, G, L, log2L, SV, a.stride, tid, nthr,
-                 (RealT<C>)a.tau2_scale, lay);
+                 (RealT<C>)a.tau2_scale, lay, tax);
     fft_lines_rt<true>(sm, tw, L, log2L, nslots, tid, nthr, lay);
   }
   __syncthreads();

@@ -133,7 +133,8 @@ struct dso_ctx {
   bool tables_valid = false;
   double tables_dt = 0.0;
   void* Utab = nullptr;      // [na][S(S+1)/2][P] complex, context precision
-  void* tau = nullptr;       // [nb][P] complex, context precision
+  void* tau = nullptr;       // [nb][P] complex, context precision; separable: [nb][sum_d n_d]
+  int kin_mode = DSO_KINETIC_JOINT;  // dso_set_kinetic_mode
   double* tau_a = nullptr;   // [na] potential coefficient * dt
   int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
   void* tw[14] = {};         // per log2 L (L <= 8192), context precision
@@ -176,6 +177,27 @@ int ilog2(int64_t v) {
   int l = 0;
   while ((1LL << l) < v) ++l;
   return l;
+}
+
+// The kinetic step as one phase per axis (each axis's phase applied between
+// its own forward and inverse FFT, PASS_TAX) instead of one phase of the
+// whole grid.  Needs unsplit axes (the momentum index along each line is
+// that axis's own) and at least two of them.
+bool kin_axes(const dso_ctx* c) {
+  return c->kin_mode == DSO_KINETIC_AXES && c->Dv == c->D && c->D >= 2;
+}
+
+// Length of one separable kinetic table (all axes) and the offset of axis d.
+int64_t axis_table_len(const dso_ctx* c) {
+  int64_t n = 0;
+  for (int d = 0; d < c->D; ++d) n += c->n[d];
+  return n;
+}
+
+int64_t axis_table_off(const dso_ctx* c, int d) {
+  int64_t n = 0;
+  for (int e = 0; e < d; ++e) n += c->n[e];
+  return n;
 }
 
 void drop_graph(dso_ctx* c) {
@@ -330,10 +352,17 @@ cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& n
   const int NP = c->S * (c->S + 1) / 2;
   a.U1 = p.u1 >= 0 ? at(c->Utab, (size_t)p.u1 * NP * c->P, es) : nullptr;
   a.U2 = p.u2 >= 0 ? at(c->Utab, (size_t)p.u2 * NP * c->P, es) : nullptr;
-  a.tau = p.tb >= 0 ? at(c->tau, (size_t)p.tb * c->P, es) : nullptr;
-  a.tau2 = p.tb2 >= 0 ? at(c->tau, (size_t)p.tb2 * c->P, es) : nullptr;
   a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
-  a.tau2_scale = (double)c->P;
+  if (p.flags & PASS_TAX) {  // this axis's phase: [nb][sum_d n_d] tables, 1/L folded in
+    const size_t len = (size_t)axis_table_len(c), off = (size_t)axis_table_off(c, p.axis);
+    a.tau = p.tb >= 0 ? at(c->tau, (size_t)p.tb * len + off, es) : nullptr;
+    a.tau2 = p.tb2 >= 0 ? at(c->tau, (size_t)p.tb2 * len + off, es) : nullptr;
+    a.tau2_scale = (double)L;
+  } else {
+    a.tau = p.tb >= 0 ? at(c->tau, (size_t)p.tb * c->P, es) : nullptr;
+    a.tau2 = p.tb2 >= 0 ? at(c->tau, (size_t)p.tb2 * c->P, es) : nullptr;
+    a.tau2_scale = (double)c->P;
+  }
   a.tw = c->tw[ilog2(L)];
   if (!a.tw) return cudaErrorInvalidValue;  // no twiddle table for this line length
   a.P = c->P;
@@ -366,7 +395,7 @@ cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& n
   a.tau_base = c->tau;
   a.psi_elems = (long long)c->B * c->S * c->P;
   a.u_elems = (long long)c->B * c->n_vtab * NP * c->P;
-  a.tau_elems = (long long)c->n_ttab * c->P;
+  a.tau_elems = (long long)c->n_ttab * (kin_axes(c) ? axis_table_len(c) : c->P);
   a.dec0 = c->dec0;
   a.ctas_per_sm = c->cps[p.axis][which];
   a.pdl = c->pdl;
@@ -389,6 +418,7 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   if (variant == 3 && p.u1 >= 0 && p.tb >= 0) return cudaErrorInvalidConfiguration;  // 1-D passes
+  if ((variant == 2 || variant == 3) && (p.flags & PASS_TAX)) return cudaErrorInvalidConfiguration;
   if (variant == 2 || variant == 3) {
     const int Wi = (int)(stride < a.G ? stride : a.G);
     const int Go = a.G / Wi;
@@ -439,7 +469,54 @@ void t_action(const dso_ctx* c, std::vector<Pass>& out, bool standalone_f0, int 
   for (int d = D - 2; d >= 1; --d) out.push_back(mkpass(d, 1, PASS_INV_FIRST));
 }
 
+// Separable kinetic step (kin_axes), D >= 2: every kinetic action is one
+// pass [F_d T_d I_d] per axis, each applying that axis's phase between its own
+// FFTs; the potential action joins the axis-0 pass of the next kinetic action.
+// VTV:  [V F0 T0 I0] [F1 T1 I1] .. [F_{D-1} T_{D-1} I_{D-1}] per substep,
+//   final [V]; at step boundaries the last V of a step and the first of the
+//   next share one pass.
+// TVT:  [F0 T0 I0] .. in the first substep of the first step, then [V F0 T0
+//   I0] ..; at step boundaries both kinetic coefficients' phases act in one
+//   pass per axis; the final kinetic action is [V F0 T0 I0] .. with the
+//   step's last coefficients.
+void t_action_axes(const dso_ctx* c, std::vector<Pass>& out, int u1, int u2, int tb, int tb2) {
+  const int f = PASS_FWD | PASS_T | PASS_TAX;
+  out.push_back(mkpass(0, u1 >= 0 ? c->S : 1, f, u1, u2, tb, tb2));
+  for (int d = 1; d < c->Dv; ++d) out.push_back(mkpass(d, 1, f, -1, -1, tb, tb2));
+}
+
+std::vector<Pass> step_passes_axes(const dso_ctx* c, bool first) {
+  std::vector<Pass> out;
+  const std::vector<int>& ia = c->coeffs.ia;
+  const std::vector<int>& ib = c->coeffs.ib;
+  const int NB = (int)c->coeffs.b.size();
+  const int last = (int)c->coeffs.a.size() - 1;
+  for (int j = 0; j < NB; ++j) {
+    if (c->elementary == DSO_VTV) {
+      const bool merge = j == 0 && !first;
+      t_action_axes(c, out, merge ? ia[last] : ia[j], merge ? ia[0] : -1, ib[j], -1);
+    } else {
+      const bool merge = j == 0 && !first;
+      const int uv = (j == 0) ? (first ? -1 : ib[NB - 1]) : ib[j - 1];
+      t_action_axes(c, out, uv, -1, merge ? ia[last] : ia[j], merge ? ia[0] : -1);
+    }
+  }
+  return out;
+}
+
+std::vector<Pass> final_passes_axes(const dso_ctx* c) {
+  std::vector<Pass> out;
+  const int last = (int)c->coeffs.a.size() - 1;
+  const int NB = (int)c->coeffs.b.size();
+  if (c->elementary == DSO_VTV)
+    out.push_back(mkpass(0, c->S, 0, c->coeffs.ia[last]));
+  else
+    t_action_axes(c, out, c->coeffs.ib[NB - 1], -1, c->coeffs.ia[last], -1);
+  return out;
+}
+
 std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
+  if (kin_axes(c)) return step_passes_axes(c, first);
   std::vector<Pass> out;
   const std::vector<int>& ia = c->coeffs.ia;
   const std::vector<int>& ib = c->coeffs.ib;
@@ -479,6 +556,7 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
 }
 
 std::vector<Pass> final_passes(const dso_ctx* c) {
+  if (kin_axes(c)) return final_passes_axes(c);
   std::vector<Pass> out;
   const int last = (int)c->coeffs.a.size() - 1;
   const int NB = (int)c->coeffs.b.size();
@@ -548,7 +626,8 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   const int na = (int)vco.size(), nb = (int)tco.size();
   const int NP = c->S * (c->S + 1) / 2;
   CK(cudaMalloc(&c->Utab, (size_t)c->B * na * NP * c->P * c->esz()));
-  CK(cudaMalloc(&c->tau, (size_t)nb * c->P * c->esz()));
+  const bool sep = kin_axes(c);
+  CK(cudaMalloc(&c->tau, (size_t)nb * (sep ? axis_table_len(c) : c->P) * c->esz()));
   CK(cudaMalloc(&c->tau_a, (size_t)na * sizeof(double)));
   c->n_vtab = na;
   c->n_ttab = nb;
@@ -566,7 +645,9 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   CK(cudaMalloc(&dcoef, coef.size() * sizeof(double)));
   cudaError_t e = cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
                                   c->stream);
-  if (e == cudaSuccess) e = launch_kinetic_tables(c->tau, c->prec == DSO_FP32, dcoef, nb, vlayout(c), c->P, c->stream);
+  if (e == cudaSuccess)
+    e = sep ? launch_axis_kinetic_tables(c->tau, c->prec == DSO_FP32, dcoef, nb, c->D, c->n, c->stream)
+            : launch_kinetic_tables(c->tau, c->prec == DSO_FP32, dcoef, nb, vlayout(c), c->P, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(dcoef);
   CK(e);
@@ -587,8 +668,8 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 // stream of jobs of one shape (a serving loop) tunes once.
 // The key holds everything that fixes the pass kinds and their lines: the
 // grid, S (which with the pass limits fixes the virtual axes), the batch,
-// precision, elementary method and device.
-using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int>;
+// precision, elementary method, device and the form of the kinetic step.
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int>;
 struct TuneVal {
   int G[DSO_MAX_VAXES][2];
   int variant[DSO_MAX_VAXES][2];
@@ -599,7 +680,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 TuneKey tune_key(const dso_ctx* c) {
   return TuneKey(c->D, c->n[0], c->n[1], c->n[2], c->S, c->B, c->prec, c->elementary, c->device, c->max_line,
-                 c->max_tile);
+                 c->max_tile, kin_axes(c) ? 1 : 0);
 }
 
 dso_status autotune_tiles(dso_ctx* c) {
@@ -693,10 +774,10 @@ dso_status autotune_tiles(dso_ctx* c) {
         if (only >= 0 && var != only) continue;
         if (var != 0 && var != 4 && c->prec == DSO_FP32) continue;  // variants 1-3 are FP64 only
         if (var == 3 && both_tables) continue;
-        if (var == 4 && (greg == 0 || lines % greg)) continue;
-        for (long long G = var == 4 ? greg : 1; G <= (var == 4 ? greg : gmax) && G <= lines && err == cudaSuccess;
-             G *= 2) {
-          if (var != 4 && any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
+        const bool reg = var == 4;
+        if (reg && (greg == 0 || lines % greg)) continue;
+        for (long long G = reg ? greg : 1; G <= (reg ? greg : gmax) && G <= lines && err == cudaSuccess; G *= 2) {
+          if (!reg && any_whole && (SV * G * (L / 8)) % 32 != 0) continue;
           if (var == 1 && !axis_pass_pq_supported(L, SV, (int)G)) continue;
           if (var == 2 && !axis_pass_tma_supported(L, SV, (int)G)) continue;
           if (var == 3 && !axis_pass_tmap_supported(L, SV, (int)G)) continue;
@@ -1713,6 +1794,18 @@ int dso_tuned_plan(const dso_ctx* c, char* out, int cap) {
   return (int)s.size();
 }
 
+dso_status dso_set_kinetic_mode(dso_ctx* c, int mode) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (mode != DSO_KINETIC_JOINT && mode != DSO_KINETIC_AXES)
+    return fail(DSO_EINVAL, "mode must be DSO_KINETIC_JOINT or DSO_KINETIC_AXES");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_tables(c);
+  c->kin_mode = mode;
+  c->tuned = false;  // other pass kinds
+  return DSO_OK;
+}
+
 dso_status dso_set_pass_limits(dso_ctx* c, int max_line, int max_tile) {
   if (!c) return fail(DSO_EINVAL, "null context");
   if (max_line < 8 || max_line > DSO_MAX_LINE || (max_line & (max_line - 1)) || max_tile < 16 || max_tile > 8192 ||
@@ -2086,7 +2179,7 @@ bool axis_pass_tmap_supported(int L, int SV, int G) {
 int axis_pass_reg_lines(int L, int SV) {
   if (SV < 1 || SV > DSO_MAX_SURFACES || (L != 32 && L != 64 && L != 128)) return 0;
   const int tpl = L == 32 ? RegPlan<32>::TPL : L == 64 ? RegPlan<64>::TPL : RegPlan<128>::TPL;
-  return (SV == 1 ? reg_threads<1>() : reg_threads<2>()) / tpl;
+  return reg_threads<1>() / tpl;
 }
 
 bool axis_pass_pq_supported(int L, int SV, int G) {

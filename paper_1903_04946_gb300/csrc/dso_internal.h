@@ -136,6 +136,11 @@ std::vector<double> host_kinetic_coefficients(int D, const double* qmin, const d
 // correction for the low part.  Output is double2, or float2 rounded once.
 cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double* coef, int nb, const VLayout& v, long long P,
                                   cudaStream_t st);
+// Separable kinetic tables: tau[u][off_d + k], the phase of axis d alone at
+// momentum index k (natural FFT order) for every unique coefficient, 1/n_d
+// folded in; off_d = n_0 + .. + n_{d-1}.
+cudaError_t launch_axis_kinetic_tables(void* tau, bool fp32, const double* coef, int nb, int D, const int64_t* n,
+                                       cudaStream_t st);
 // Twiddles of a split axis of n = n1 * n2 points: xtw[k1 * n2 + i2] =
 // exp(-2 pi i (k1 i2 mod n) / n) (sincospi of an exact argument), double2
 // or rounded once to float2.

@@ -11,6 +11,8 @@ enum PassFlags : int {
   PASS_T = 4,          // kinetic phase then inverse FFT after the forward FFT
   PASS_XTW = 8,        // the axis is the first factor of a split axis: conj twiddles
                        // before the inverse FFT, twiddles after the forward FFT
+  PASS_TAX = 16,       // with PASS_T: the phase of this axis alone, a table of L entries
+                       // indexed by the momentum index along the line (separable kinetic step)
 };
 
 // Complex arrays are double2 (FP64 path) or float2 (FP32 storage mode).
@@ -18,9 +20,10 @@ struct PassArgs {
   void* psi;               // [S][P] wavefunction (in/out)
   const void* U1;          // [S(S+1)/2][P] potential unitary, or null
   const void* U2;          // second potential unitary, or null
-  const void* tau;         // [P] kinetic phase (1/P folded in), or null
+  const void* tau;         // [P] kinetic phase (1/P folded in), or null; with PASS_TAX
+                           // [L] the phase of this axis (1/L folded in)
   const void* tau2;        // second kinetic phase (TVT step boundary), or null;
-                           // its folded 1/P is undone by tau2_scale = P (exact)
+                           // its folded 1/P (1/L) is undone by tau2_scale = P (L), exact
   const void* tw;          // [L] exp(-2 pi i m / L), m = 0..L-1
   long long P;             // grid points per surface
   long long stride;        // element stride of the axis (product of later axes)
@@ -33,7 +36,7 @@ struct PassArgs {
   int ua;                  // unique-coefficient index of U1 (TMA variant)
   int ub;                  // unique-coefficient index of tau (TMA variant)
   int* err;                // device flag set when a bounded wait gives up
-  double tau2_scale;       // P: both kinetic tables carry 1/P, one inverse FFT runs
+  double tau2_scale;       // P (L): both kinetic tables carry 1/P (1/L), one inverse FFT runs
   int fp32;                // 1: complex arrays are float2 (FP32 storage mode)
   int nbatch;              // independent jobs sharing the grid: psi is [nbatch][S][P]
   long long u_batch_stride;  // elements between one job's potential tables and the next

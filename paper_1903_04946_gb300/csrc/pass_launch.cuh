@@ -180,6 +180,7 @@ cudaError_t launch_variant(int variant, const PassArgs& a, long long ntiles, uns
     return cudaErrorInvalidConfiguration;
   }
   if (variant != 0 && a.fp32) return cudaErrorInvalidConfiguration;  // FP64 only
+  if (variant != 0 && (a.flags & PASS_TAX)) return cudaErrorInvalidConfiguration;  // grid-sized tables only
   if (variant != 0 && (a.flags & PASS_XTW)) return cudaErrorInvalidConfiguration;  // split axes: tile kernel
   if (variant == 1) {
     if constexpr (SV * L / 8 <= 256) return launch_pq<L, SV>(a, ntiles, queue, st);

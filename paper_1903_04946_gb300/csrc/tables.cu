@@ -104,6 +104,52 @@ cudaError_t launch_kinetic_tables(void* tau, bool fp32, const double* coef, int 
   return cudaGetLastError();
 }
 
+// tau[u][off_d + k]: the phase of axis d alone, exp(i C_d kk^2) / n_d, with
+// the angle carried as hi + lo as in kinetic_table_kernel (one term).
+struct AxisSizes {
+  int64_t n[3];
+};
+
+template <typename OutC>
+__global__ void axis_kinetic_table_kernel(OutC* __restrict__ tau, const double* __restrict__ coef, int D,
+                                          AxisSizes ax, long long len) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= len) return;
+  const int u = blockIdx.y;
+  int d = 0;
+  long long k = idx;
+  while (d + 1 < D && k >= ax.n[d]) k -= ax.n[d++];
+  const long long n = ax.n[d];
+  const long long kk = (k < n / 2) ? k : k - n;
+  const double x = (double)(kk * kk);
+  const double ch = coef[(u * D + d) * 2], cl = coef[(u * D + d) * 2 + 1];
+  double hi = ch * x;
+  double lo = fma(ch, x, -hi) + cl * x;
+  const double r = hi + lo;  // renormalise
+  lo = lo - (r - hi);
+  hi = r;
+  double sn, cs;
+  sincos(hi, &sn, &cs);
+  const double inv_n = 1.0 / (double)n;  // a power of two: exact
+  store_c(&tau[(size_t)u * len + idx], inv_n * (cs - sn * lo), inv_n * (sn + cs * lo));
+}
+
+cudaError_t launch_axis_kinetic_tables(void* tau, bool fp32, const double* coef, int nb, int D, const int64_t* n,
+                                       cudaStream_t st) {
+  AxisSizes ax{};
+  long long len = 0;
+  for (int d = 0; d < D && d < 3; ++d) {
+    ax.n[d] = n[d];
+    len += n[d];
+  }
+  dim3 grid((unsigned)((len + 255) / 256), (unsigned)nb);
+  if (fp32)
+    axis_kinetic_table_kernel<<<grid, 256, 0, st>>>((float2*)tau, coef, D, ax, len);
+  else
+    axis_kinetic_table_kernel<<<grid, 256, 0, st>>>((double2*)tau, coef, D, ax, len);
+  return cudaGetLastError();
+}
+
 // Split-axis twiddles w_n^(k1 i2) in the [n1][n2] layout of the passes.
 template <typename OutC>
 __global__ void split_twiddle_kernel(OutC* __restrict__ xtw, int64_t n1, int64_t n2) {
