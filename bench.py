@@ -293,7 +293,7 @@ def run_gpu(args):
     ctx = dso.Context(device=device, stream=stream, precision=dso.DSO_FP32 if fp32 else dso.DSO_FP64)
     ctx.load_problem(pr)
     dso.dso_set_scheme(ctx.ctx, ORDER, scheme_code())
-    kin_mode = {"joint": dso.DSO_KINETIC_JOINT, "axes": dso.DSO_KINETIC_AXES}[args.kinetic]
+    kin_mode = {"auto": dso.DSO_KINETIC_AUTO, "joint": dso.DSO_KINETIC_JOINT, "axes": dso.DSO_KINETIC_AXES}[args.kinetic]
     dso.dso_set_kinetic_mode(ctx.ctx, kin_mode)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
 
@@ -497,7 +497,9 @@ def run_gpu(args):
                 "config": config_dict({"l2": "flushed before every timed step (256 MiB write outside the "
                                              "per-step CUDA events)",
                                        "substeps_per_step": nsub, "grid_points": pts,
-                                       "kinetic_step": "per axis" if args.kinetic == "axes" else "joint"}),
+                                       "kinetic_step": "per axis" if (args.kinetic == "axes" or
+                                                                      (args.kinetic == "auto" and fp32))
+                                       else "joint"}),
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
                 "graph_replay": graph}
         if cpu is not None:
@@ -531,7 +533,7 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
     tables read per grid point (the loaded potential entries and, for the
     joint kinetic step, its phase, 8 B each) -- and the error against the
     FP64 path.  The value is the library's default form of the kinetic step
-    (joint); the per-axis form (DSO_KINETIC_AXES) is timed beside it."""
+    in FP32 (per axis, DSO_KINETIC_AUTO); the joint form is timed beside it."""
     import numpy as np
     import torch
 
@@ -573,8 +575,8 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
         gbs = bytes_step / (ms * 1e-3) / 1e9
         return ms, bytes_step, gbs, plan
 
-    ms, bytes_step, gbs, plan = timed(dso.DSO_KINETIC_JOINT)
-    ms_x, bytes_x, gbs_x, _ = timed(dso.DSO_KINETIC_AXES)
+    ms, bytes_step, gbs, plan = timed(dso.DSO_KINETIC_AUTO)
+    ms_j, bytes_j, gbs_j, _ = timed(dso.DSO_KINETIC_JOINT)
     c32 = dso.Context(pr, device=device, order=order, scheme=dso.DSO_TRIPLE_JUMP, precision=dso.DSO_FP32)
     c64 = dso.Context(pr, device=device, order=order, scheme=dso.DSO_TRIPLE_JUMP, precision=dso.DSO_FP64)
     c32.propagate(check_steps * dt, dt)
@@ -588,16 +590,15 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
                         "(FP64 angles, coefficients and reductions), triple jump order 4, dt = 2000/128 a.u.",
             "value": pts * nsub / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "substeps_per_step": nsub, "l2": "flushed before every timed step",
-            "kinetic_step": "joint (phase of the whole grid between full transforms)", "plan": plan,
+            "kinetic_step": "per axis (one pass per axis, potential joined to the axis-0 pass)", "plan": plan,
             "roofline": {"bound": "hbm", "bytes_per_step": bytes_step, "achieved": round(gbs, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
                          "bytes": "algorithmic: 32 B per amplitude-substep (psi read + written by two fused "
-                                  "passes) + 8 B per grid point per table entry read (4 potential entries, "
-                                  "1 kinetic phase)"},
-            "per_axis_kinetic_step": {"ms_per_step": ms_x, "value": pts * nsub / (ms_x * 1e-3),
-                                      "roofline_frac": round(gbs_x / peak, 4),
-                                      "bytes": "as above without the kinetic phase (per-axis tables of "
-                                               "sum_d n_d entries)"},
+                                  "passes) + 8 B per grid point per table entry read (4 potential entries; "
+                                  "the per-axis kinetic tables hold sum_d n_d entries, not counted)"},
+            "joint_kinetic_step": {"ms_per_step": ms_j, "value": pts * nsub / (ms_j * 1e-3),
+                                   "roofline_frac": round(gbs_j / peak, 4),
+                                   "bytes": "as above plus one kinetic phase (8 B) per grid point"},
             "error_vs_fp64": {"steps": check_steps, "rel_l2": err, "norm_drift": float(abs(n32 - 1.0)),
                               "reference": "FP64 GPU path, same input and steps"}}
 
@@ -843,8 +844,8 @@ def main():
                     help="skip the sub-records (FP32 precision mode, time to 1e-10, serving)")
     ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
     ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
-    ap.add_argument("--kinetic", default="joint", choices=["joint", "axes"],
-                    help="form of the kinetic step (dso_set_kinetic_mode)")
+    ap.add_argument("--kinetic", default="auto", choices=["auto", "joint", "axes"],
+                    help="form of the kinetic step (dso_set_kinetic_mode); auto: per axis in FP32, joint in FP64")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="after the warm-up, run this many steps inside cudaProfilerStart/Stop and exit "
                          "(for ncu --profile-from-start off)")

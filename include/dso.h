@@ -63,7 +63,7 @@ enum { DSO_HOST = 0, DSO_DEVICE = 1 };
 enum { DSO_FP64 = 0, DSO_FP32 = 1 };
 enum { DSO_TRIPLE_JUMP = 0, DSO_SUZUKI = 1, DSO_OPTIMAL = 2 };
 enum { DSO_VTV = 0, DSO_TVT = 1, DSO_VT = 2, DSO_TV = 3 };
-enum { DSO_KINETIC_JOINT = 0, DSO_KINETIC_AXES = 1 };
+enum { DSO_KINETIC_AUTO = -1, DSO_KINETIC_JOINT = 0, DSO_KINETIC_AXES = 1 };
 
 /* Limits of this build. */
 #define DSO_MAX_DIM 3
@@ -349,20 +349,21 @@ dso_status dso_set_pass_limits(dso_ctx* ctx, int max_line, int max_tile);
  * diagonal mass matrix of Eq. (diab_mol_ham), T = sum_d p_d^2 / (2 m_d) and
  * the per-axis factors commute, so U_T is the product over the axes of
  * exp(-i dt p_d^2 / (2 m_d)), each diagonal in that axis's own momentum
- * representation.  DSO_KINETIC_JOINT (the default) transforms all axes
- * forward, applies the phase of the whole grid and transforms back (four
- * passes per substep on a 3-D grid, one table of P entries per unique
- * kinetic coefficient).  DSO_KINETIC_AXES applies each axis's phase between
- * that axis's own forward and inverse FFT, in one pass per axis with the
- * potential step joined to the axis-0 pass (three passes per substep on a
- * 3-D grid, tables of n_0 + .. + n_{D-1} entries); the result agrees with the
- * joint form to round-off.  On GB300 the joint form is the faster one in
- * both precisions (its FFT-only passes are short and its potential pass
- * overlaps the potential tables' loads with an inverse FFT); the per-axis
- * form saves the kinetic tables' memory.  Grids with one axis, or with an
- * axis split into two virtual axes (dso_set_pass_limits), always use the
- * joint form.  Any other mode returns DSO_EINVAL.  Drops the context's tables
- * and tuning; the state is kept. */
+ * representation.  DSO_KINETIC_JOINT transforms all axes forward, applies
+ * the phase of the whole grid and transforms back (four passes per substep
+ * on a 3-D grid, one table of P entries per unique kinetic coefficient).
+ * DSO_KINETIC_AXES applies each axis's phase between that axis's own forward
+ * and inverse FFT, in one pass per axis with the potential step joined to
+ * the axis-0 pass (three passes per substep on a 3-D grid, tables of
+ * n_0 + .. + n_{D-1} entries, D - 1 more phase multiplications per
+ * amplitude); the result agrees with the joint form to round-off.
+ * DSO_KINETIC_AUTO (the default) takes the per-axis form in DSO_FP32 mode,
+ * whose passes are bound by memory traffic (one wavefunction round trip per
+ * substep fewer), and the joint form in DSO_FP64 mode, whose passes are bound
+ * by FP64 arithmetic.  Grids with one axis, or with an axis split into two
+ * virtual axes (dso_set_pass_limits), always use the joint form.  Any other
+ * mode returns DSO_EINVAL.  Drops the context's tables and tuning; the state
+ * is kept. */
 dso_status dso_set_kinetic_mode(dso_ctx* ctx, int mode);
 
 /* Batch slots (continuous batching).  A batch advances many jobs -- each a

@@ -22,7 +22,7 @@ DSO_FP64, DSO_FP32 = 0, 1
 DSO_TRIPLE_JUMP, DSO_SUZUKI, DSO_OPTIMAL = 0, 1, 2
 SCHEME_CODES = {"triple_jump": DSO_TRIPLE_JUMP, "suzuki": DSO_SUZUKI, "optimal": DSO_OPTIMAL}
 DSO_VTV, DSO_TVT, DSO_VT, DSO_TV = 0, 1, 2, 3
-DSO_KINETIC_JOINT, DSO_KINETIC_AXES = 0, 1
+DSO_KINETIC_AUTO, DSO_KINETIC_JOINT, DSO_KINETIC_AXES = -1, 0, 1
 
 EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",

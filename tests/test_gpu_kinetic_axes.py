@@ -8,7 +8,7 @@ applies the phase of the whole grid between full transforms) within the
 FP64 parity bound, for VTV and TVT, merged step boundaries and graph-replayed
 middle steps; the tile and register kernels must agree bit for bit on it;
 batches and batch slots must give each job its result alone; and the
-default must stay the joint form, in both precisions."""
+default (DSO_KINETIC_AUTO) must take it in FP32 only."""
 import numpy as np
 import pytest
 
@@ -118,20 +118,23 @@ def test_axes_batch_slot_equals_alone(dso):
     batch.close()
 
 
-def test_default_form_and_fp32(dso):
-    """Without the call both precisions use the joint form; the per-axis
-    form in FP32 storage mode stays within the FP32 bound of the oracle."""
+def test_default_form_by_precision(dso):
+    """Without the call FP64 uses the joint form and FP32 the per-axis one;
+    both FP32 forms stay within the FP32 bound of the oracle."""
     pr = synth.pyrazine_like(seed=70, n=(16, 16, 32))
     for fp32 in (False, True):
         ctx = dso.Context(pr, order=2, precision=dso.DSO_FP32 if fp32 else dso.DSO_FP64)
         ctx.propagate(50.0, 50.0)
         kinds = dso.dso_profile_steps(ctx.ctx, 50.0, 1)
         ctx.close()
-        assert not any(k["flags"] & 16 for k in kinds)
-    x32, k32 = _run(dso, [pr], 2, "triple_jump", 2 * 50.0, 50.0, dso.DSO_KINETIC_AXES, fp32=True)
-    assert all(f & 16 for _, f, _, _ in k32 if f & 4)
+        if fp32:
+            assert all(k["flags"] & 16 for k in kinds if k["flags"] & 4)
+        else:
+            assert not any(k["flags"] & 16 for k in kinds)
     ref = oracle_propagate(pr, 2, "triple_jump", 2 * 50.0, 50.0)
-    assert rel_l2(x32.astype(np.complex128), ref) < 1e-5
+    for mode in (dso.DSO_KINETIC_AUTO, dso.DSO_KINETIC_JOINT):
+        x32, _ = _run(dso, [pr], 2, "triple_jump", 2 * 50.0, 50.0, mode, fp32=True)
+        assert rel_l2(x32.astype(np.complex128), ref) < 1e-5
 
 
 def test_one_axis_and_split_grids_keep_the_joint_form(dso):
