@@ -345,6 +345,19 @@ dso_status dso_fp64_issue_rate(int device, double* inst_per_s);
  * paper has no counterpart. */
 dso_status dso_set_pass_limits(dso_ctx* ctx, int max_line, int max_tile);
 
+/* Step boundaries.  In a symmetric composition the first and last a~
+ * coefficients belong to the same operator (the potential for DSO_VTV, the
+ * kinetic step for DSO_TVT), so the last action of one time step and the
+ * first of the next act back to back and form one action with coefficient
+ * a~_last + a~_0, the merge of adjacent actions of Sec. II F applied across
+ * the step boundary.  merged = 1 (the default) gives that action a table of
+ * its own (one more table when a~_last + a~_0 is not already a unique value)
+ * and applies it once; merged = 0 applies the two tables one after the other
+ * in one pass.  The two agree to round-off; the first step and the final
+ * action of a propagation are not affected.  Any other value returns
+ * DSO_EINVAL.  Drops the context's tables and tuning; the state is kept. */
+dso_status dso_set_boundary_merge(dso_ctx* ctx, int merged);
+
 /* Form of the kinetic step U_T(dt) = exp(-i dt T(p)) of Sec. II G.  With the
  * diagonal mass matrix of Eq. (diab_mol_ham), T = sum_d p_d^2 / (2 m_d) and
  * the per-axis factors commute, so U_T is the product over the axes of

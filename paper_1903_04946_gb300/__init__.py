@@ -33,7 +33,7 @@ EXPORTS = (
     "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer", "dso_set_pass_limits",
     "dso_batch_create", "dso_batch_destroy", "dso_batch_add", "dso_batch_step", "dso_batch_sync",
     "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count", "dso_batch_busy",
-    "dso_set_kinetic_mode",
+    "dso_set_kinetic_mode", "dso_set_boundary_merge",
 )
 
 _lib = None
@@ -85,6 +85,7 @@ def load(path: str = LIB):
         "dso_psi_device_pointer": (i32, [vp, ctypes.POINTER(vp)]),
         "dso_set_pass_limits": (i32, [vp, i32, i32]),
         "dso_set_kinetic_mode": (i32, [vp, i32]),
+        "dso_set_boundary_merge": (i32, [vp, i32]),
         "dso_batch_create": (i32, [ctypes.POINTER(vp), i32, i32, vp]),
         "dso_batch_destroy": (None, [vp]),
         "dso_batch_add": (i32, [vp, vp, dbl, dbl, ctypes.POINTER(i32)]),
@@ -323,6 +324,10 @@ def dso_set_pass_limits(ctx, max_line, max_tile):
 
 def dso_set_kinetic_mode(ctx, mode):
     _check(load().dso_set_kinetic_mode(ctx, int(mode)), "dso_set_kinetic_mode")
+
+
+def dso_set_boundary_merge(ctx, merged):
+    _check(load().dso_set_boundary_merge(ctx, int(merged)), "dso_set_boundary_merge")
 
 
 def dso_batch_create(device: int = 0, precision: int = DSO_FP64, stream=None):

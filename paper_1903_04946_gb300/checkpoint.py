@@ -6,13 +6,18 @@ the pruned coefficients a~, b~, their index arrays and the elementary
 method.  Resuming checks the digest, so a run cannot continue with another
 scheme by mistake, and loads psi into a context built for the same problem.
 
-With the VTV method resuming is exact.  A propagation split at a step
-boundary applies the same operations in the same order as the uninterrupted
-one: the last potential action of the first part, then the first of the
-second.  The tests check that the two results are bitwise equal.  With TVT
-the uninterrupted run applies the two kinetic actions of a step boundary
-between one forward and one inverse FFT, the split run returns to position
-space in between, so the results agree to round-off (tested to 1e-13).
+By default the uninterrupted run applies the last a~ action of a step and
+the first of the next as one action with coefficient a~_last + a~_0
+(dso_set_boundary_merge), where a run split at that boundary applies the two
+in turn, so the results agree to round-off (tested to 1e-13).  With the
+unmerged boundary (dso_set_boundary_merge(ctx, 0)) and the VTV method
+resuming is exact: the split run applies the same operations in the same
+order as the uninterrupted one, the last potential action of the first part
+and then the first of the second; the tests check that the two results are
+bitwise equal.  With TVT the uninterrupted run applies the two kinetic
+actions of a step boundary between one forward and one inverse FFT, the
+split run returns to position space in between, so the results agree to
+round-off.
 
     ck = checkpoint.capture(ctx, order, scheme, elementary, steps_done, dt)
     checkpoint.save("run.npz", ck)

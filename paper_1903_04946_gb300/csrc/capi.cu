@@ -135,6 +135,7 @@ struct dso_ctx {
   void* Utab = nullptr;      // [na][S(S+1)/2][P] complex, context precision
   void* tau = nullptr;       // [nb][P] complex, context precision; separable: [nb][sum_d n_d]
   int kin_mode = DSO_KINETIC_AUTO;  // dso_set_kinetic_mode
+  int boundary_merged = 1;          // dso_set_boundary_merge: one table for a~_last + a~_0
   double* tau_a = nullptr;   // [na] potential coefficient * dt
   int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
   void* tw[14] = {};         // per log2 L (L <= 8192), context precision
@@ -202,6 +203,32 @@ int64_t axis_table_off(const dso_ctx* c, int d) {
   int64_t n = 0;
   for (int e = 0; e < d; ++e) n += c->n[e];
   return n;
+}
+
+// Step boundaries.  A symmetric composition's last a~ action of one step and
+// first of the next act back to back on the same operator (the potential in
+// VTV, the kinetic step in TVT), so they are one action with coefficient
+// a~_last + a~_0 (Sec. II F merges adjacent actions of one operator the same
+// way).  With boundary_merged that action has a table of its own: the index
+// of a~_last + a~_0 among the unique a~ values (equal to a relative 1e-12, as
+// the unique values are found), or one past them when it is new.  -1: the two
+// actions are applied one after the other in one pass.
+int merged_a_index(const dso_ctx* c) {
+  if (!c->boundary_merged || c->coeffs.a.empty()) return -1;
+  const double m = c->coeffs.a.front() + c->coeffs.a.back();
+  const std::vector<double>& u = c->coeffs.a_unq;
+  for (size_t j = 0; j < u.size(); ++j)
+    if (std::fabs(u[j] - m) <= 1e-12 * std::fabs(m)) return (int)j;
+  return (int)u.size();
+}
+
+// The a~ values with tables: the unique ones, plus the merged boundary value
+// when it is new.
+std::vector<double> a_table_values(const dso_ctx* c) {
+  std::vector<double> v = c->coeffs.a_unq;
+  const int mi = merged_a_index(c);
+  if (mi == (int)v.size()) v.push_back(c->coeffs.a.front() + c->coeffs.a.back());
+  return v;
 }
 
 void drop_graph(dso_ctx* c) {
@@ -498,11 +525,19 @@ std::vector<Pass> step_passes_axes(const dso_ctx* c, bool first) {
   for (int j = 0; j < NB; ++j) {
     if (c->elementary == DSO_VTV) {
       const bool merge = j == 0 && !first;
-      t_action_axes(c, out, merge ? ia[last] : ia[j], merge ? ia[0] : -1, ib[j], -1);
+      const int mi = merged_a_index(c);
+      if (merge && mi >= 0)
+        t_action_axes(c, out, mi, -1, ib[j], -1);
+      else
+        t_action_axes(c, out, merge ? ia[last] : ia[j], merge ? ia[0] : -1, ib[j], -1);
     } else {
       const bool merge = j == 0 && !first;
       const int uv = (j == 0) ? (first ? -1 : ib[NB - 1]) : ib[j - 1];
-      t_action_axes(c, out, uv, -1, merge ? ia[last] : ia[j], merge ? ia[0] : -1);
+      const int mi = merged_a_index(c);
+      if (merge && mi >= 0)
+        t_action_axes(c, out, uv, -1, mi, -1);
+      else
+        t_action_axes(c, out, uv, -1, merge ? ia[last] : ia[j], merge ? ia[0] : -1);
     }
   }
   return out;
@@ -531,8 +566,9 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
     for (int j = 0; j < NB; ++j) {
       int u1 = ia[j], u2 = -1;
       if (j == 0 && !first) {
-        u1 = ia[last];
-        u2 = ia[0];
+        const int mi = merged_a_index(c);
+        u1 = mi >= 0 ? mi : ia[last];
+        u2 = mi >= 0 ? -1 : ia[0];
       }
       if (D == 1) {
         out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, u1, u2, ib[j]));
@@ -546,8 +582,10 @@ std::vector<Pass> step_passes(const dso_ctx* c, bool first) {
   }
   // TVT: kinetic coefficients a~ (tables by I^a), potential b~ (tables by I^b)
   for (int j = 0; j < NB; ++j) {
-    const int tb = (j == 0 && !first) ? ia[last] : ia[j];
-    const int tb2 = (j == 0 && !first) ? ia[0] : -1;
+    const int mi = merged_a_index(c);
+    const bool merge = j == 0 && !first;
+    const int tb = merge ? (mi >= 0 ? mi : ia[last]) : ia[j];
+    const int tb2 = (merge && mi < 0) ? ia[0] : -1;
     const int uv = (j == 0) ? (first ? -1 : ib[NB - 1]) : ib[j - 1];
     if (D == 1) {
       out.push_back(mkpass(0, c->S, PASS_FWD | PASS_T, uv, -1, tb, tb2));
@@ -625,8 +663,9 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   if (st != DSO_OK) return st;
   // VTV: the potential takes the a~ coefficients and the kinetic step the b~;
   // TVT swaps them.
-  const std::vector<double>& vco = (c->elementary == DSO_VTV) ? c->coeffs.a_unq : c->coeffs.b_unq;
-  const std::vector<double>& tco = (c->elementary == DSO_VTV) ? c->coeffs.b_unq : c->coeffs.a_unq;
+  const std::vector<double> avals = a_table_values(c);
+  const std::vector<double>& vco = (c->elementary == DSO_VTV) ? avals : c->coeffs.b_unq;
+  const std::vector<double>& tco = (c->elementary == DSO_VTV) ? c->coeffs.b_unq : avals;
   const int na = (int)vco.size(), nb = (int)tco.size();
   const int NP = c->S * (c->S + 1) / 2;
   CK(cudaMalloc(&c->Utab, (size_t)c->B * na * NP * c->P * c->esz()));
@@ -1818,6 +1857,17 @@ int dso_tuned_plan(const dso_ctx* c, char* out, int cap) {
   if ((int)s.size() + 1 > cap) return fail(DSO_EINVAL, "dso_tuned_plan: buffer too small");
   std::memcpy(out, s.c_str(), s.size() + 1);
   return (int)s.size();
+}
+
+dso_status dso_set_boundary_merge(dso_ctx* c, int merged) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (merged != 0 && merged != 1) return fail(DSO_EINVAL, "merged must be 0 or 1");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_tables(c);
+  c->boundary_merged = merged;
+  c->tuned = false;  // other pass kinds
+  return DSO_OK;
 }
 
 dso_status dso_set_kinetic_mode(dso_ctx* c, int mode) {

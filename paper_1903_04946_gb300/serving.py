@@ -69,16 +69,16 @@ class Job:
 
 def footprint_bytes(problem, order, scheme=DSO_TRIPLE_JUMP, esz=16) -> int:
     """Device bytes one job holds: psi and the autotuning/observables work
-    copy, the FP64 potential, the potential unitaries (one per unique a~) and
-    kinetic phases (one per unique b~), the twiddles of split axes and small
-    buffers."""
+    copy, the FP64 potential, the potential unitaries (one per unique a~, plus
+    the merged step-boundary coefficient) and kinetic phases (one per unique
+    b~), the twiddles of split axes and small buffers."""
     S, P = problem.S, problem.points
     NP = S * (S + 1) // 2
     a, b, ia, ib, na, nb = dso_scheme_coefficients(order, scheme)
     # four-step twiddles of every axis the library splits (longer than a pass
     # line, or an axis 0 whose S surfaces exceed one tile)
     split = sum(int(x) for d, x in enumerate(problem.n) if x > 4096 or (d == 0 and S * x > 8192))
-    return int(2 * S * P * esz + NP * P * 8 + na * NP * P * esz + nb * P * esz + split * esz + (1 << 20))
+    return int(2 * S * P * esz + NP * P * 8 + (na + 1) * NP * P * esz + nb * P * esz + split * esz + (1 << 20))
 
 
 def job_cost_seconds(job, rate=1.2e9) -> float:

@@ -4,20 +4,24 @@ The timed workload is the 3-D three-surface pyrazine-like model on a 64^3
 grid per surface, complex128, Suzuki order 6 (25 substeps per step),
 dt = 2000/128 a.u., built by the benchmark's own workload function.  Three
 time steps exercise every pass kind of the timed run: the first step's
-[V F0], the merged step boundary [I0 VV F0], the CUDA-graph replay of the
-middle steps and the final [I0 V].  The GPU result is compared with the FP64
-oracle element by element (relative L2 <= 1e-12 and every element within
-1e-11 of the largest amplitude) in four launch configurations:
+[V F0], the merged step boundary (one potential action with coefficient
+a~_last + a~_0), the CUDA-graph replay of the middle steps and the final
+[I0 V].  The GPU result is compared with the FP64 oracle element by element
+(relative L2 <= 1e-12 and every element within 1e-11 of the largest
+amplitude) in four launch configurations:
 
 * the product path with the autotuned kernel plan, on a caller stream as in
   the benchmark (one propagate call of three steps: graph replay);
-* the benchmark's timed call pattern (one propagate call per step);
+* the benchmark's timed call pattern (one propagate call per step, whose
+  step boundaries are the two actions of the unmerged form);
 * the autotuned plan forced through DSO_PLAN (the configuration a profiler
   run reproduces);
 * every kernel variant forced on all pass kinds.
 
-The results of all configurations must also agree with each other bitwise:
-they run the same arithmetic.
+The results of the configurations that run the same arithmetic must agree
+bitwise; the per-step calls agree bitwise with one call whose boundary is
+unmerged (dso_set_boundary_merge(ctx, 0)) and to round-off with the merged
+one.
 """
 import os
 
@@ -82,8 +86,15 @@ def test_bench_call_pattern(setup, monkeypatch):
     out = ctx.psi()
     ctx.close()
     assert_parity(out, ref)
+    whole = _bench_context(dso, bench, pr, stream)
+    dso.dso_set_boundary_merge(whole.ctx, 0)
+    whole.propagate(NSTEPS * bench.DT, bench.DT)
+    unmerged = whole.psi()
+    whole.close()
+    assert np.array_equal(out, unmerged)
     if "graph" in setup_cache:
-        assert np.array_equal(out, setup_cache["graph"])
+        g = setup_cache["graph"]
+        assert np.sqrt(np.sum(np.abs(out - g) ** 2) / np.sum(np.abs(g) ** 2)) < 1e-13
 
 
 def test_forced_tuned_plan(setup, monkeypatch):
@@ -103,16 +114,18 @@ def test_forced_tuned_plan(setup, monkeypatch):
     assert np.array_equal(out, setup_cache["graph"])
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_every_variant_full_size(setup, monkeypatch, variant):
     dso, bench, pr, ref = setup
     import torch
     # the same variant on every pass kind that supports it (4 lines per tile,
-    # 2 resident CTAs per SM for the persistent TMA variant)
+    # 16 for the register-resident variant, 2 resident CTAs per SM for the
+    # persistent TMA variant)
     entries = []
     for axis in range(3):
         for staged in (0, 1):
-            entries.append(f"{axis},{staged},{variant},4,{2 if variant == 3 else 0};")
+            g = 16 if variant == 4 else 4
+            entries.append(f"{axis},{staged},{variant},{g},{2 if variant == 3 else 0};")
     monkeypatch.setenv("DSO_PLAN", "".join(entries))
     stream = torch.cuda.Stream()
     ctx = _bench_context(dso, bench, pr, stream)
