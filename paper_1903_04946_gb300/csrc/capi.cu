@@ -741,6 +741,11 @@ dso_status autotune_tiles(dso_ctx* c) {
       const int SV = w ? c->S : 1;
       if (lines % g) continue;
       if (v == 4 ? g != axis_pass_reg_lines((int)L, SV) : g > axis_pass_max_tile_lines((int)L, SV)) continue;
+      if (v == 4) {
+        long long stride = 1;
+        for (int e = d + 1; e < c->Dv; ++e) stride *= c->nv[e];
+        if (!axis_pass_reg_supported((int)L, SV, c->prec == DSO_FP32, stride)) continue;
+      }
       if (c->prec == DSO_FP32 && v != 0 && v != 4) continue;
       if ((v == 1 && !axis_pass_pq_supported((int)L, SV, g)) || (v == 2 && !axis_pass_tma_supported((int)L, SV, g)) ||
           (v == 3 && (!axis_pass_tmap_supported((int)L, SV, g) || c->Dv == 1)))
@@ -2250,6 +2255,13 @@ bool axis_pass_tmap_supported(int L, int SV, int G) {
   const int np = SV > 1 ? SV * (SV + 1) / 2 : 1;
   const long long smem = 2LL * (SV + np) * G * L * 16 + (long long)L * 16 + 192;
   return SV * G * (L / 8) <= 256 && smem <= 220 * 1024 && encode_fn() != nullptr;
+}
+
+bool axis_pass_reg_supported(int L, int SV, bool fp32, long long stride) {
+  const int g = axis_pass_reg_lines(L, SV);
+  if (g == 0 || (stride != 1 && stride < g)) return false;
+  const int vpt = L == 128 ? 16 : 8;
+  return SV * vpt * (fp32 ? 2 : 4) <= 96;  // the amplitudes fit a thread's registers (reg_fits)
 }
 
 int axis_pass_reg_lines(int L, int SV) {

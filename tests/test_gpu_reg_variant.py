@@ -147,3 +147,22 @@ def test_reg_variant_surface_counts(monkeypatch, S, grid, fp32):
         assert rel_l2(b.astype(np.complex128), ref) < 1e-5
     else:
         assert_parity(b, ref)
+
+
+def test_forced_plan_skips_shapes_the_variant_cannot_take(monkeypatch):
+    """DSO_PLAN entries naming variant 4 where it does not apply (FP64
+    128-point lines of three surfaces: too many amplitudes for a thread's
+    registers; a 32-point axis of stride 8, narrower than its tile) are
+    ignored: those kinds keep the tile kernel and the propagation runs."""
+    dso = require_gpu()
+    pr = synth.pyrazine_like(seed=49, n=(128, 32, 8))
+    plan = "0,1,4,16,0;1,0,4,32,0;"
+    monkeypatch.setenv("DSO_PLAN", plan)
+    ctx = dso.Context(pr, order=2)
+    ctx.propagate(50.0, 25.0)
+    out = ctx.psi()
+    kinds = _kinds(dso.dso_tuned_plan(ctx.ctx))
+    ctx.close()
+    assert kinds[(0, 1)][0] == 0 and kinds[(1, 0)][0] == 0
+    monkeypatch.delenv("DSO_PLAN")
+    assert_parity(out, oracle_propagate(pr, 2, "triple_jump", 50.0, 25.0))
