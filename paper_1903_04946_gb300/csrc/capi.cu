@@ -158,6 +158,7 @@ struct dso_ctx {
   int variant[DSO_MAX_VAXES][2] = {};
   int cps[DSO_MAX_VAXES][2] = {};  // resident CTAs per SM of the persistent variants (0: as many as fit)
   int pdl = 1;               // programmatic dependent launch between passes (DSO_PDL=0: off)
+  bool prev_tile = true;     // the last pass launched on the stream ran the tile kernel (variant 0)
   int wait_probe = 0;        // dso_set_wait_probe: polls of the TMA variant's diagnostic wait (0: off)
   int max_line = DSO_MAX_LINE;  // dso_set_pass_limits: longest pass line,
   int max_tile = 8192;          // and most points of the S surfaces of an axis-0 line
@@ -474,6 +475,13 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
     if (!ok) return cudaErrorInvalidConfiguration;
   }
   c->launches += 1;
+  // Programmatic dependent launch only between two passes of the other
+  // variants: the tile kernel's many small CTAs measured slower with it on
+  // either side (64^3 x 3 FP64: all tile passes 4.46 -> 5.93 ms per step; a
+  // tile kinetic pass between register-resident ones 4.45 -> 4.9 ms), while a
+  // step of TMA and register-resident passes gains from it (4.54 -> 4.31 ms).
+  if (variant == 0 || c->prev_tile) a.pdl = 0;
+  c->prev_tile = variant == 0;
   return launch_axis_pass(L, p.SV, variant, a, ntiles, c->queue, &maps, c->stream);
 }
 
@@ -798,6 +806,11 @@ dso_status autotune_tiles(dso_ctx* c) {
       if (r.axis == q.axis && (r.SV == 1) == (q.SV == 1)) seen = true;
     if (!seen) reps.push_back(q);
   }
+  TuneVal alt[2];  // whole-step candidates: tile kernel everywhere; the other variants where they apply
+  std::memcpy(alt[0].G, c->G, sizeof(c->G));
+  std::memcpy(alt[0].variant, c->variant, sizeof(c->variant));
+  std::memcpy(alt[0].cps, c->cps, sizeof(c->cps));
+  alt[1] = alt[0];
   for (const Pass& rp : reps) {
     if (err != cudaSuccess) break;
     Pass p = rp;
@@ -811,9 +824,9 @@ dso_status autotune_tiles(dso_ctx* c) {
       bool any_whole = false;
       for (long long G = 1; G <= gmax && G <= lines; G *= 2)
         if ((SV * G * (L / 8)) % 32 == 0) any_whole = true;
-      float best = 1e30f, best0 = 1e30f;
+      float best = 1e30f, best0 = 1e30f, bestN = 1e30f;
       int bestG = c->G[d][which], bestV = c->variant[d][which], bestC = c->cps[d][which];
-      int bestG0 = bestG;
+      int bestG0 = bestG, bestGN = bestG, bestVN = -1, bestCN = 0;
       // DSO_VARIANT=v restricts the search to one kernel variant (testing)
       const char* fv = getenv("DSO_VARIANT");
       const int only = (fv && fv[0] >= '0' && fv[0] <= '4') ? fv[0] - '0' : -1;
@@ -858,6 +871,12 @@ dso_status autotune_tiles(dso_ctx* c) {
               best0 = ms;
               bestG0 = (int)G;
             }
+            if (err == cudaSuccess && var != 0 && ms < bestN) {
+              bestN = ms;
+              bestGN = (int)G;
+              bestVN = var;
+              bestCN = c->cps[d][which];
+            }
             const char* vb = getenv("DSO_TUNE_VERBOSE");
             if (vb && vb[0] == '1' && err == cudaSuccess)
               fprintf(stderr, "dso autotune: axis %d SV %d flags %d variant %d G %lld cps %d: %.2f us\n", d, SV,
@@ -865,20 +884,65 @@ dso_status autotune_tiles(dso_ctx* c) {
           }
         }
       }
-      // The tile kernel is kept unless another variant is faster by more than
-      // 3 %: the passes are timed alone, ten launches on warm caches, and a
-      // variant within that margin has measured slower inside the step (FP64
-      // [F2 T I2] at 64^3: 62.7 against 60.5 us for a 1 % gain when timed alone).
-      if (bestV != 0 && best0 < 1e30f && best > 0.97f * best0) {
-        best = best0;
-        bestG = bestG0;
-        bestV = 0;
-        bestC = 0;
-      }
       c->G[d][which] = bestG;
       c->variant[d][which] = bestV;
       c->cps[d][which] = bestC;
+      // the kind's entries in the two other whole-step candidates
+      alt[0].G[d][which] = best0 < 1e30f ? bestG0 : bestG;
+      alt[0].variant[d][which] = best0 < 1e30f ? 0 : bestV;
+      alt[0].cps[d][which] = best0 < 1e30f ? 0 : bestC;
+      alt[1].G[d][which] = bestVN >= 0 ? bestGN : bestG;
+      alt[1].variant[d][which] = bestVN >= 0 ? bestVN : bestV;
+      alt[1].cps[d][which] = bestVN >= 0 ? bestCN : bestC;
     }
+  }
+  // Whole-step choice.  The passes are timed alone above, but a pass's cost
+  // inside the step depends on its neighbours (programmatic dependent launch
+  // overlaps the tail of one pass of the persistent, TMA or
+  // register-resident variants with the start of the next, and is not used
+  // next to the tile kernel).  So three candidate plans -- the fastest
+  // variant of every kind, the tile kernel everywhere, and the fastest of the
+  // other variants wherever one applies -- are timed over host-launched
+  // middle steps, and the fastest is kept.
+  if (err == cudaSuccess && !getenv("DSO_VARIANT")) {
+    TuneVal cand[3];
+    std::memcpy(cand[0].G, c->G, sizeof(c->G));
+    std::memcpy(cand[0].variant, c->variant, sizeof(c->variant));
+    std::memcpy(cand[0].cps, c->cps, sizeof(c->cps));
+    cand[1] = alt[0];
+    cand[2] = alt[1];
+    const std::vector<Pass> mid = step_passes(c, false);
+    float bestStep = 1e30f;
+    int pick = 0;
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+      bool same = false;
+      for (int j = 0; j < k; ++j)
+        same = same || (std::memcmp(&cand[j], &cand[k], sizeof(TuneVal)) == 0);
+      if (same) continue;
+      std::memcpy(c->G, cand[k].G, sizeof(c->G));
+      std::memcpy(c->variant, cand[k].variant, sizeof(c->variant));
+      std::memcpy(c->cps, cand[k].cps, sizeof(c->cps));
+      for (const Pass& p : mid)  // warm-up
+        if (err == cudaSuccess) err = run_pass(c, p);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3; ++r)
+        for (const Pass& p : mid)
+          if (err == cudaSuccess) err = run_pass(c, p);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      const char* vb = getenv("DSO_TUNE_VERBOSE");
+      if (vb && vb[0] == '1' && err == cudaSuccess)
+        fprintf(stderr, "dso autotune: whole-step candidate %d: %.2f us per middle step\n", k, ms * 1000.f / 3.f);
+      if (err == cudaSuccess && ms < bestStep) {
+        bestStep = ms;
+        pick = k;
+      }
+    }
+    std::memcpy(c->G, cand[pick].G, sizeof(c->G));
+    std::memcpy(c->variant, cand[pick].variant, sizeof(c->variant));
+    std::memcpy(c->cps, cand[pick].cps, sizeof(c->cps));
   }
   c->psi = keep;
   c->launches = launches + (c->launches - launches);
