@@ -1,5 +1,6 @@
 // axis_pass_reg.cuh -- register-resident axis pass for lines of 32, 64 and
-// 128 points: the FFT-only passes and the fused kinetic pass [F T I].
+// 128 points: FFT-only passes, kinetic passes [F T I] and, for passes that
+// stage all S surfaces, the potential step ([I0 V F0], [V F0 T0 I0], [V]).
 //
 // The tile kernel (axis_pass.cuh) moves a tile through shared memory once per
 // Stockham stage, and for FP32 data its passes issue ~110 thread instructions
@@ -329,21 +330,51 @@ __host__ __device__ constexpr bool reg_fits() {
   return SV * RegPlan<L>::VPT * (int)(sizeof(C) / 4) <= 96;
 }
 
-// One tile: reg_lines<L, SV>() line positions of the SV staged surfaces (SV = 1:
-// one surface; SV = S: all surfaces of one job).  Optional inverse FFT,
-// potential step(s), forward FFT, kinetic phase(s) and inverse FFT, as the
-// tile kernel; no split-axis twiddles.  Shared memory: the exchange buffer
-// (G lines), then, for a pass with a potential step, the staging buffer of
-// the unitary's entries.  The potential tables do not change during a
-// propagation, so their copies are issued before the wait for the previous
-// pass and land while this tile's wavefunction loads and inverse FFT run.
+// The kinetic phase(s) at this thread's elements, as apply_kinetic: from a
+// table of the grid (element at line + off(m)) or of this axis alone
+// (element t + TPL m, PASS_TAX).
+template <int L, int SV, typename C>
+__device__ __forceinline__ void kinetic_reg(C (&v)[SV][RegPlan<L>::VPT], const PassArgs& a, long long line, int sh,
+                                            int t) {
+  constexpr int TPL = RegPlan<L>::TPL, VPT = RegPlan<L>::VPT;
+  const bool tax = (a.flags & PASS_TAX) != 0;
+  const long long tline = tax ? 0 : line;
+  const int tsh = tax ? 0 : sh;
+  const C* tau = reinterpret_cast<const C*>(a.tau) + tline;
+#pragma unroll
+  for (int m = 0; m < VPT; ++m) {
+    const C ph = __ldg(&tau[(unsigned)(t + TPL * m) << tsh]);
+#pragma unroll
+    for (int s = 0; s < SV; ++s) v[s][m] = cmul(v[s][m], ph);
+  }
+  if (a.tau2) {
+    const C* tau2 = reinterpret_cast<const C*>(a.tau2) + tline;
+#pragma unroll
+    for (int m = 0; m < VPT; ++m) {
+      C ph = __ldg(&tau2[(unsigned)(t + TPL * m) << tsh]);
+      if ((RealT<C>)a.tau2_scale != (RealT<C>)1) ph = cscale(ph, (RealT<C>)a.tau2_scale);
+#pragma unroll
+      for (int s = 0; s < SV; ++s) v[s][m] = cmul(v[s][m], ph);
+    }
+  }
+}
+
+// One tile: reg_lines<L, SV>() line positions of SV surfaces of one job,
+// starting at its surface s_first.  Optional inverse FFT, potential step(s),
+// forward FFT, kinetic phase(s) and inverse FFT, as the tile kernel; no
+// split-axis twiddles.  With `pot` the potential tables' packed entries
+// u0 .. u0 + SV(SV+1)/2 - 1 of each point form the SV x SV unitary (dec0:
+// its first row and column vanish, see matvec_sym).  Shared memory: the
+// exchange buffer (G lines), then the staging buffer of the unitary's
+// entries.  The potential tables do not change during a propagation, so their
+// copies are issued before the wait for the previous pass and land while
+// this tile's wavefunction loads and inverse FFT run.
 template <int L, int SV, bool CONTIG, typename C>
-__global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_reg_kernel(PassArgs a) {
+__device__ __forceinline__ void reg_tile(const PassArgs& a, const TileJob& tj, int s_first, int u0, int dec0,
+                                         bool pot, C* sm) {
   constexpr int TPL = RegPlan<L>::TPL, VPT = RegPlan<L>::VPT, G = reg_lines<L, SV>(), NT = reg_threads<SV>();
   constexpr bool WL = CONTIG;  // a line's threads in one warp (contiguous lines)
   using LY = RegLayout<L, WL>;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
   const int tid = threadIdx.x;
   // contiguous lines: a line's TPL threads are consecutive lanes (a warp
   // barrier in the exchange); strided lines: consecutive lanes take
@@ -352,7 +383,6 @@ __global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_
   // measured 1.45x slower on 128-point FP32 lines.
   const int g = WL ? tid / TPL : tid % G;
   const int t = WL ? tid % TPL : tid / G;
-  const TileJob tj = split_tile(blockIdx.x, SV, a);
   const TileGeom tg = make_geom(tj.tile, a);
   // Element m of this thread's part of the line sits at line + off(m); the
   // offsets within a line are below P <= 2^30 and kept in 32 bits.
@@ -367,10 +397,9 @@ __global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_
   }
   C* ln = sm + g * LY::LS;
   C* us = sm + G * LY::LS;
-  const size_t uoff = (size_t)tj.job * a.u_batch_stride + line;
-  if (SV > 1 && a.U1)  // the host sets U1/U2 only for passes that stage all S surfaces
-    stage_potential<L, SV, NT>(us, reinterpret_cast<const C*>(a.U1) + uoff, a.P, t, sh, a.dec0, tid);
-  C* psi = reinterpret_cast<C*>(a.psi) + (size_t)tj.surf0 * a.P + line;
+  const size_t uoff = (size_t)tj.job * a.u_batch_stride + (size_t)u0 * a.P + line;
+  if (pot) stage_potential<L, SV, NT>(us, reinterpret_cast<const C*>(a.U1) + uoff, a.P, t, sh, dec0, tid);
+  C* psi = reinterpret_cast<C*>(a.psi) + (size_t)(tj.surf0 + s_first) * a.P + line;
   const C* tw = reinterpret_cast<const C*>(a.tw);
   C v[SV][VPT];
   pdl_wait();  // psi is the previous pass's output
@@ -380,54 +409,35 @@ __global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_
     for (int m = 0; m < VPT; ++m) v[s][m] = psi[(size_t)s * a.P + ((unsigned)(t + TPL * m) << sh)];
   }
   pdl_trigger();
-  // The pass's steps in order: inverse FFT, potential step(s), forward FFT,
-  // kinetic phase(s), inverse FFT.  With several surfaces they run as one
-  // loop whose body holds one FFT (the sign a runtime value), so that the
-  // straight-line code -- run once per tile -- stays small: unrolled, the
-  // three-surface body's instruction fetches stalled its warps as often as
-  // its memory loads did.  One surface keeps the unrolled sequence (fewer
-  // registers).
   const int f = a.flags;
-  const bool pot = SV > 1 && a.U1;
-  constexpr int J0 = SV == 1 ? 1 : 0;  // step 0 of the one-surface sequence is unrolled below
-  if constexpr (SV == 1) {
+  auto potential = [&]() {
+    const unsigned after = potential_reg<L, SV, NT>(v, us, dec0, tid);
+    if (a.U2) {  // the second table goes through the same slots of this thread, copied once they are read
+      stage_potential<L, SV, NT>(us + after, reinterpret_cast<const C*>(a.U2) + uoff, a.P, t, sh, dec0, tid);
+      potential_reg<L, SV, NT>(v, us, dec0, tid);
+    }
+  };
+  if constexpr (SV == 1) {  // one surface: the steps unrolled (fewer registers)
     if (f & PASS_INV_FIRST) fft_reg<L, SV, WL>(v, ln, t, tw, (RealT<C>)-1);
+    if (pot) potential();
     if (f & PASS_FWD) fft_reg<L, SV, WL>(v, ln, t, tw, (RealT<C>)1);
-  }
-#pragma unroll(SV == 1 ? 4 : 1)
-  for (int j = J0; j < 5; ++j) {
-    if (SV == 1 && j == 2) continue;  // the forward FFT ran above
-    const bool fft = (j == 0 && (f & PASS_INV_FIRST)) || (j == 2 && (f & PASS_FWD)) ||
-                     (j == 4 && (f & PASS_FWD) && (f & PASS_T));
-    if (fft) {
-      fft_reg<L, SV, WL>(v, ln, t, tw, j == 2 ? (RealT<C>)1 : (RealT<C>)-1);
-    } else if (j == 1 && pot) {
-      const unsigned after = potential_reg<L, SV, NT>(v, us, a.dec0, tid);
-      if (a.U2) {  // the second table goes through the same slots of this thread, copied once they are read
-        stage_potential<L, SV, NT>(us + after, reinterpret_cast<const C*>(a.U2) + uoff, a.P, t, sh, a.dec0, tid);
-        potential_reg<L, SV, NT>(v, us, a.dec0, tid);
-      }
-    } else if (j == 3 && (f & PASS_FWD) && (f & PASS_T)) {  // the kinetic phase(s), as apply_kinetic
-      // a table of the grid (element at line + off(m)) or of this axis alone (element t + TPL m)
-      const bool tax = (f & PASS_TAX) != 0;
-      const long long tline = tax ? 0 : line;
-      const int tsh = tax ? 0 : sh;
-      const C* tau = reinterpret_cast<const C*>(a.tau) + tline;
-#pragma unroll
-      for (int m = 0; m < VPT; ++m) {
-        const C ph = __ldg(&tau[(unsigned)(t + TPL * m) << tsh]);
-#pragma unroll
-        for (int s = 0; s < SV; ++s) v[s][m] = cmul(v[s][m], ph);
-      }
-      if (a.tau2) {
-        const C* tau2 = reinterpret_cast<const C*>(a.tau2) + tline;
-#pragma unroll
-        for (int m = 0; m < VPT; ++m) {
-          C ph = __ldg(&tau2[(unsigned)(t + TPL * m) << tsh]);
-          if ((RealT<C>)a.tau2_scale != (RealT<C>)1) ph = cscale(ph, (RealT<C>)a.tau2_scale);
-#pragma unroll
-          for (int s = 0; s < SV; ++s) v[s][m] = cmul(v[s][m], ph);
-        }
+    if ((f & PASS_FWD) && (f & PASS_T)) kinetic_reg<L, SV>(v, a, line, sh, t);
+    if ((f & PASS_FWD) && (f & PASS_T)) fft_reg<L, SV, WL>(v, ln, t, tw, (RealT<C>)-1);
+  } else {
+    // With several surfaces the steps run as one loop whose body holds one
+    // FFT (the sign a runtime value), so that the straight-line code -- run
+    // once per tile -- stays small: unrolled, the three-surface body's
+    // instruction fetches stalled its warps as often as its memory loads did.
+#pragma unroll 1
+    for (int j = 0; j < 5; ++j) {
+      const bool fft = (j == 0 && (f & PASS_INV_FIRST)) || (j == 2 && (f & PASS_FWD)) ||
+                       (j == 4 && (f & PASS_FWD) && (f & PASS_T));
+      if (fft) {
+        fft_reg<L, SV, WL>(v, ln, t, tw, j == 2 ? (RealT<C>)1 : (RealT<C>)-1);
+      } else if (j == 1 && pot) {
+        potential();
+      } else if (j == 3 && (f & PASS_FWD) && (f & PASS_T)) {
+        kinetic_reg<L, SV>(v, a, line, sh, t);
       }
     }
   }
@@ -441,6 +451,34 @@ __global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_
 #pragma unroll
     for (int m = 0; m < VPT; ++m) psi[(size_t)s * a.P + ((unsigned)(t + TPL * m) << sh_st)] = v[s][m];
   }
+}
+
+// One tile of reg_lines<L, SV>() line positions of the SV staged surfaces
+// (SV = 1: one surface; SV = S: all surfaces of one job).
+template <int L, int SV, bool CONTIG, typename C>
+__global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_reg_kernel(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const TileJob tj = split_tile(blockIdx.x, SV, a);
+  // the host sets U1/U2 only for passes that stage all S surfaces
+  reg_tile<L, SV, CONTIG>(a, tj, 0, 0, a.dec0, SV > 1 && a.U1, reinterpret_cast<C*>(smraw));
+}
+
+// Passes that stage all S > 2 surfaces with surface 0 decoupled (dec0: the
+// unitary is block diagonal, U_00 and the S-1 x S-1 block of the others):
+// every tile is two CTAs, the even one transforming surface 0 with the
+// diagonal entry U_00 (packed entry 0), the odd one surfaces 1..S-1 with the
+// block (packed entries S .. S(S+1)/2 - 1, in the packed order of an S-1
+// matrix).  The products are those of matvec_sym with dec0, bit for bit, and
+// each CTA holds the amplitudes of fewer surfaces, so more CTAs share an SM.
+template <int L, int S, bool CONTIG, typename C>
+__global__ void __launch_bounds__(reg_threads<S>(), 3) axis_pass_reg_split_kernel(PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const TileJob tj = split_tile(blockIdx.x >> 1, S, a);
+  C* sm = reinterpret_cast<C*>(smraw);
+  if ((blockIdx.x & 1) == 0)
+    reg_tile<L, 1, CONTIG>(a, tj, 0, 0, 0, a.U1 != nullptr, sm);
+  else
+    reg_tile<L, S - 1, CONTIG>(a, tj, 1, S, 0, a.U1 != nullptr, sm);
 }
 
 // Shared memory of a tile: the exchange buffer and, with a potential step,

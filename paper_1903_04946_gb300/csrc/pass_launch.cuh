@@ -145,28 +145,42 @@ cudaError_t launch_tmap(const PassArgs& a, const TmaMaps* maps, long long ntiles
 // positions of SV surfaces per CTA, contiguous lines or lines of one outer row.
 template <int L, int SV, typename C>
 cudaError_t launch_reg_t(const PassArgs& a, long long ntiles, cudaStream_t st) {
-  if constexpr (!reg_fits<L, SV, C>()) {
+  constexpr bool split_fits = SV >= 3 && reg_fits<L, (SV >= 3 ? SV - 1 : 1), C>();
+  if constexpr (!reg_fits<L, SV, C>() && !split_fits) {
     return cudaErrorInvalidConfiguration;
   } else {
-    static bool attr_set[2][64] = {};
+    static bool attr_set[2][2][64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     const bool contig = a.stride_log2 == 0;
     if (a.G != reg_lines<L, SV>() || (SV == 1 && (a.U1 || a.U2)) || (a.flags & PASS_XTW) ||
         (!contig && a.stride_log2 < a.G_log2))
       return cudaErrorInvalidConfiguration;
-    constexpr int NP = SV * (SV + 1) / 2;
-    const int np_staged = (SV > 1 && a.U1) ? (SV > 2 && a.dec0 ? NP - (SV - 1) : NP) : 0;
+    // surface 0 decoupled: a CTA for it and one for the block of the others
+    const bool split = split_fits && a.dec0 && a.U1;
+    if (!split && !reg_fits<L, SV, C>()) return cudaErrorInvalidConfiguration;
+    constexpr int NP = SV * (SV + 1) / 2, NPB = SV * (SV - 1) / 2;
+    const int np_staged = split ? NPB : (SV > 1 && a.U1) ? (SV > 2 && a.dec0 ? NP - (SV - 1) : NP) : 0;
     const size_t smem = reg_smem_bytes<L, SV>(contig, sizeof(C) == 8, np_staged);
     const size_t smem_max = reg_smem_bytes<L, SV>(contig, sizeof(C) == 8, SV > 1 ? NP : 0);
     if (smem_max > 227 * 1024) return cudaErrorInvalidConfiguration;
-    void (*k)(PassArgs) = contig ? axis_pass_reg_kernel<L, SV, true, C> : axis_pass_reg_kernel<L, SV, false, C>;
-    if (!attr_set[contig][dev]) {
+    void (*k)(PassArgs) = nullptr;
+    if constexpr (split_fits) {
+      if (split)
+        k = contig ? axis_pass_reg_split_kernel<L, (SV >= 3 ? SV : 3), true, C>
+                   : axis_pass_reg_split_kernel<L, (SV >= 3 ? SV : 3), false, C>;
+    }
+    if constexpr (reg_fits<L, SV, C>()) {
+      if (!split) k = contig ? axis_pass_reg_kernel<L, SV, true, C> : axis_pass_reg_kernel<L, SV, false, C>;
+    }
+    if (!k) return cudaErrorInvalidConfiguration;
+    if (!attr_set[split][contig][dev]) {
       const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
       if (e != cudaSuccess) return e;
-      attr_set[contig][dev] = true;
+      attr_set[split][contig][dev] = true;
     }
-    const cudaError_t e = launch_k(k, (unsigned)ntiles, reg_threads<SV>(), smem, st, a.pdl != 0, a);
+    const cudaError_t e =
+        launch_k(k, (unsigned)(split ? 2 * ntiles : ntiles), reg_threads<SV>(), smem, st, a.pdl != 0, a);
     return e != cudaSuccess ? e : cudaGetLastError();
   }
 }
