@@ -752,7 +752,7 @@ dso_status autotune_tiles(dso_ctx* c) {
       if (v == 4) {
         long long stride = 1;
         for (int e = d + 1; e < c->Dv; ++e) stride *= c->nv[e];
-        if (!axis_pass_reg_supported((int)L, SV, c->prec == DSO_FP32, stride)) continue;
+        if (!axis_pass_reg_supported((int)L, SV, c->prec == DSO_FP32, stride, c->dec0 != 0)) continue;
       }
       if (c->prec == DSO_FP32 && v != 0 && v != 4) continue;
       if ((v == 1 && !axis_pass_pq_supported((int)L, SV, g)) || (v == 2 && !axis_pass_tma_supported((int)L, SV, g)) ||
@@ -2321,11 +2321,13 @@ bool axis_pass_tmap_supported(int L, int SV, int G) {
   return SV * G * (L / 8) <= 256 && smem <= 220 * 1024 && encode_fn() != nullptr;
 }
 
-bool axis_pass_reg_supported(int L, int SV, bool fp32, long long stride) {
+bool axis_pass_reg_supported(int L, int SV, bool fp32, long long stride, bool dec0) {
   const int g = axis_pass_reg_lines(L, SV);
   if (g == 0 || (stride != 1 && stride < g)) return false;
-  const int vpt = L == 128 ? 16 : 8;
-  return SV * vpt * (fp32 ? 2 : 4) <= 96;  // the amplitudes fit a thread's registers (reg_fits)
+  const int vpt = L == 128 ? 16 : 8, w = fp32 ? 2 : 4;
+  // the amplitudes fit a thread's registers (reg_fits), all SV surfaces or,
+  // with surface 0 decoupled, the block of the others (the split form)
+  return SV * vpt * w <= 96 || (dec0 && SV >= 3 && (SV - 1) * vpt * w <= 96);
 }
 
 int axis_pass_reg_lines(int L, int SV) {

@@ -89,8 +89,8 @@ bool axis_pass_tmap_supported(int L, int SV, int G);
 // tile lines of the register-resident variant, 0 where it does not apply
 int axis_pass_reg_lines(int L, int SV);
 // the register-resident variant takes lines of L points along an axis of
-// `stride` with SV surfaces staged
-bool axis_pass_reg_supported(int L, int SV, bool fp32, long long stride);
+// `stride` with SV surfaces staged (dec0: surface 0 decoupled)
+bool axis_pass_reg_supported(int L, int SV, bool fp32, long long stride, bool dec0);
 // per-SV launchers (one translation unit each)
 cudaError_t launch_axis_pass_sv1(int L, int variant, const PassArgs& a, long long ntiles, unsigned* queue,
                                  const TmaMaps* maps, cudaStream_t st);

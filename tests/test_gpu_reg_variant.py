@@ -166,3 +166,23 @@ def test_forced_plan_skips_shapes_the_variant_cannot_take(monkeypatch):
     assert kinds[(0, 1)][0] == 0 and kinds[(1, 0)][0] == 0
     monkeypatch.delenv("DSO_PLAN")
     assert_parity(out, oracle_propagate(pr, 2, "triple_jump", 50.0, 25.0))
+
+
+@pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
+def test_reg_variant_split_four_surfaces(monkeypatch, fp32):
+    """Four surfaces with surface 0 decoupled: the all-surface pass runs as
+    two CTAs per tile (surface 0 with its diagonal entry, surfaces 1-3 with
+    their 3 x 3 block); in FP64 that is the only register-resident form the
+    32-point lines fit.  Bitwise equal to the tile kernel, within the parity
+    bound of the oracle."""
+    require_gpu()
+    pr = synth.pyrazine_like(seed=50, n=(32, 64, 64), S=4)
+    a, _ = _run(monkeypatch, "0", [pr], 4, "suzuki", 2 * 25.0, 25.0, fp32=fp32)
+    b, plan = _run(monkeypatch, "4", [pr], 4, "suzuki", 2 * 25.0, 25.0, fp32=fp32)
+    _check_plan(plan, (1, 2), (0,))
+    assert np.array_equal(a, b)
+    ref = oracle_propagate(pr, 4, "suzuki", 2 * 25.0, 25.0)
+    if fp32:
+        assert rel_l2(b.astype(np.complex128), ref) < 1e-5
+    else:
+        assert_parity(b, ref)
