@@ -31,6 +31,7 @@ UNIT = "grid-pts*substeps/s"
 T_FINAL = 2000.0
 SEED = 1904
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+PLANE_MODES = {"auto": -1, "off": 0, "on": 1}  # DSO_PLANE_AUTO / _OFF / _ON
 
 # Workloads.  The default is the 64^3 three-surface FP64 propagation the
 # metric is quoted on; "precision128" is the FP32 storage-and-FFT mode on a
@@ -200,11 +201,19 @@ def pass_flops_bytes(kind, n, S, esz=16):
     if f & 4:  # the kinetic phase: a grid-sized table, or (flag 16) one of this axis alone
         flops += 6 * amps
         bytes_ += esz * (L if f & 16 else P)
+    if f & 32:  # plane pass: the same forward FFT, phase and inverse FFT along the next axis too
+        Lb = n[kind["axis"] + 1]
+        flops += 2 * (amps // Lb) * 5 * Lb * math.log2(Lb) + 6 * amps
+        bytes_ += esz * Lb
     return flops, bytes_
 
 
 def kind_name(k):
     f = k["flags"]
+    if f & 32:  # plane pass over axes d, d + 1
+        d = k["axis"]
+        return "axis_pass_plane_kernel<LA=%d,LB=%d%s> [F%d T%d I%d F%d T%d I%d]" % (
+            N_GRID[d], N_GRID[d + 1], ",float2" if W["fp32"] else "", d, d, d, d + 1, d + 1, d + 1)
     parts = []
     if f & 1:
         parts.append(f"I{k['axis']}")
@@ -225,8 +234,8 @@ def kind_name(k):
 # GPU arm
 # --------------------------------------------------------------------------
 
-KERNEL_SOURCES = ("axis_pass.cuh", "axis_pass_pq.cuh", "axis_pass_reg.cuh", "axis_pass_tma.cuh", "pass_args.h",
-                  "pass_launch.cuh")
+KERNEL_SOURCES = ("axis_pass.cuh", "axis_pass_plane.cuh", "axis_pass_pq.cuh", "axis_pass_reg.cuh",
+                  "axis_pass_tma.cuh", "pass_args.h", "pass_launch.cuh", "pass_plane.cu")
 
 
 def kernel_sources_hash() -> str:
@@ -295,6 +304,7 @@ def run_gpu(args):
     dso.dso_set_scheme(ctx.ctx, ORDER, scheme_code())
     kin_mode = {"auto": dso.DSO_KINETIC_AUTO, "joint": dso.DSO_KINETIC_JOINT, "axes": dso.DSO_KINETIC_AXES}[args.kinetic]
     dso.dso_set_kinetic_mode(ctx.ctx, kin_mode)
+    dso.dso_set_plane_pass(ctx.ctx, PLANE_MODES[args.plane])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
 
     def barrier():
@@ -590,7 +600,9 @@ def sub_precision(device, steps=10, warmup=3, check_steps=4):
                         "(FP64 angles, coefficients and reductions), triple jump order 4, dt = 2000/128 a.u.",
             "value": pts * nsub / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "substeps_per_step": nsub, "l2": "flushed before every timed step",
-            "kinetic_step": "per axis (one pass per axis, potential joined to the axis-0 pass)", "plan": plan,
+            "kinetic_step": "per axis (potential joined to the axis-0 pass; "
+                            + ("axes 1 and 2 in one plane pass)" if "plane;" in plan else "one pass per axis)"),
+            "plan": plan,
             "roofline": {"bound": "hbm", "bytes_per_step": bytes_step, "achieved": round(gbs, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
                          "bytes": "algorithmic: 32 B per amplitude-substep (psi read + written by two fused "
@@ -844,6 +856,8 @@ def main():
                     help="skip the sub-records (FP32 precision mode, time to 1e-10, serving)")
     ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
     ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
+    ap.add_argument("--plane", default="auto", choices=["auto", "on", "off"],
+                    help="plane pass of the per-axis kinetic step on the two last axes (dso_set_plane_pass)")
     ap.add_argument("--kinetic", default="auto", choices=["auto", "joint", "axes"],
                     help="form of the kinetic step (dso_set_kinetic_mode); auto: per axis in FP32, joint in FP64")
     ap.add_argument("--profile-steps", type=int, default=0,

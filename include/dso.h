@@ -64,6 +64,8 @@ enum { DSO_FP64 = 0, DSO_FP32 = 1 };
 enum { DSO_TRIPLE_JUMP = 0, DSO_SUZUKI = 1, DSO_OPTIMAL = 2 };
 enum { DSO_VTV = 0, DSO_TVT = 1, DSO_VT = 2, DSO_TV = 3 };
 enum { DSO_KINETIC_AUTO = -1, DSO_KINETIC_JOINT = 0, DSO_KINETIC_AXES = 1 };
+/* Plane pass (dso_set_plane_pass). */
+enum { DSO_PLANE_AUTO = -1, DSO_PLANE_OFF = 0, DSO_PLANE_ON = 1 };
 
 /* Limits of this build. */
 #define DSO_MAX_DIM 3
@@ -378,6 +380,24 @@ dso_status dso_set_boundary_merge(dso_ctx* ctx, int merged);
  * mode returns DSO_EINVAL.  Drops the context's tables and tuning; the state
  * is kept. */
 dso_status dso_set_kinetic_mode(dso_ctx* ctx, int mode);
+
+/* Plane pass of the per-axis kinetic step on 3-D grids.  The per-axis
+ * kinetic step (dso_set_kinetic_mode) applies exp(-i dt p_d^2 / (2 m_d)) of
+ * the two last axes d = 1, 2 in one pass each, one round trip of the
+ * wavefunction through device memory per axis.  With the plane pass both
+ * run in one: each n_1 x n_2 plane of one surface is held by one cluster of
+ * CTAs, which transforms its columns, applies axis 1's phase and transforms
+ * back, exchanges the plane through the CTAs' shared memory, and does the
+ * same along its rows (two passes per substep instead of three).  The same
+ * FFTs, phases and products in the same order: the result is bitwise that
+ * of the two passes.  Applies to 3-D grids of whole axes (none split) with
+ * n_1 and n_2 in {32, 64, 128} and the per-axis kinetic step; elsewhere, and
+ * for jobs in a batch slot, the mode has no effect.  DSO_PLANE_ON uses it
+ * wherever it applies; DSO_PLANE_OFF never; DSO_PLANE_AUTO (the default)
+ * lets the autotuner time a middle step both ways and keep the faster (with
+ * autotuning off, as DSO_PLANE_OFF).  Any other mode returns DSO_EINVAL.
+ * Drops the context's tuning; the state and tables are kept. */
+dso_status dso_set_plane_pass(dso_ctx* ctx, int mode);
 
 /* Batch slots (continuous batching).  A batch advances many jobs -- each a
  * context with its own grid, surfaces, masses, potential, scheme and state,

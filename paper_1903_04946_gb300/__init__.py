@@ -23,6 +23,7 @@ DSO_TRIPLE_JUMP, DSO_SUZUKI, DSO_OPTIMAL = 0, 1, 2
 SCHEME_CODES = {"triple_jump": DSO_TRIPLE_JUMP, "suzuki": DSO_SUZUKI, "optimal": DSO_OPTIMAL}
 DSO_VTV, DSO_TVT, DSO_VT, DSO_TV = 0, 1, 2, 3
 DSO_KINETIC_AUTO, DSO_KINETIC_JOINT, DSO_KINETIC_AXES = -1, 0, 1
+DSO_PLANE_AUTO, DSO_PLANE_OFF, DSO_PLANE_ON = -1, 0, 1
 
 EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
@@ -33,7 +34,7 @@ EXPORTS = (
     "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer", "dso_set_pass_limits",
     "dso_batch_create", "dso_batch_destroy", "dso_batch_add", "dso_batch_step", "dso_batch_sync",
     "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count", "dso_batch_busy",
-    "dso_set_kinetic_mode", "dso_set_boundary_merge",
+    "dso_set_kinetic_mode", "dso_set_boundary_merge", "dso_set_plane_pass",
 )
 
 _lib = None
@@ -86,6 +87,7 @@ def load(path: str = LIB):
         "dso_set_pass_limits": (i32, [vp, i32, i32]),
         "dso_set_kinetic_mode": (i32, [vp, i32]),
         "dso_set_boundary_merge": (i32, [vp, i32]),
+        "dso_set_plane_pass": (i32, [vp, i32]),
         "dso_batch_create": (i32, [ctypes.POINTER(vp), i32, i32, vp]),
         "dso_batch_destroy": (None, [vp]),
         "dso_batch_add": (i32, [vp, vp, dbl, dbl, ctypes.POINTER(i32)]),
@@ -328,6 +330,10 @@ def dso_set_kinetic_mode(ctx, mode):
 
 def dso_set_boundary_merge(ctx, merged):
     _check(load().dso_set_boundary_merge(ctx, int(merged)), "dso_set_boundary_merge")
+
+
+def dso_set_plane_pass(ctx, mode):
+    _check(load().dso_set_plane_pass(ctx, int(mode)), "dso_set_plane_pass")
 
 
 def dso_batch_create(device: int = 0, precision: int = DSO_FP64, stream=None):

@@ -136,6 +136,8 @@ struct dso_ctx {
   void* tau = nullptr;       // [nb][P] complex, context precision; separable: [nb][sum_d n_d]
   int kin_mode = DSO_KINETIC_AUTO;  // dso_set_kinetic_mode
   int boundary_merged = 1;          // dso_set_boundary_merge: one table for a~_last + a~_0
+  int plane_mode = DSO_PLANE_AUTO;  // dso_set_plane_pass
+  bool plane_on = false;            // the plan uses the plane pass (set by the autotuner)
   double* tau_a = nullptr;   // [na] potential coefficient * dt
   int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
   void* tw[14] = {};         // per log2 L (L <= 8192), context precision
@@ -205,6 +207,16 @@ int64_t axis_table_off(const dso_ctx* c, int d) {
   for (int e = 0; e < d; ++e) n += c->n[e];
   return n;
 }
+
+// The plane pass ([F1 T1 I1] and [F2 T2 I2] in one launch) applies to the
+// per-axis kinetic step of a 3-D grid of whole axes whose two last axes are
+// register-resident line lengths; plane_on is the tuned choice.
+bool plane_supported(const dso_ctx* c) {
+  return kin_axes(c) && c->D == 3 && c->Dv == 3 && c->plane_mode != DSO_PLANE_OFF &&
+         axis_pass_plane_supported((int)c->nv[1], (int)c->nv[2], c->prec == DSO_FP32);
+}
+
+bool plane_active(const dso_ctx* c) { return c->plane_on && plane_supported(c); }
 
 // Step boundaries.  A symmetric composition's last a~ action of one step and
 // first of the next act back to back on the same operator (the potential in
@@ -433,6 +445,12 @@ cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& n
   a.pdl = c->pdl;
   a.wait_probe = c->wait_probe;
   ntiles = (p.SV == c->S) ? (long long)c->B * (a.lines / a.G) : (long long)c->B * c->S * (a.lines / a.G);
+  if (p.flags & PASS_PLANE) {  // one plane of axes 1 and 2 of one surface per cluster
+    if (c->Dv != 3 || p.axis != 1 || p.SV != 1) return cudaErrorInvalidConfiguration;
+    a.tw2 = c->tw[ilog2(c->nv[2])];
+    if (!a.tw2) return cudaErrorInvalidValue;
+    ntiles = (long long)c->B * c->S * c->nv[0];
+  }
   return cudaSuccess;
 }
 
@@ -443,6 +461,12 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   {
     const cudaError_t e = build_pass_args(c, p, a, ntiles);
     if (e != cudaSuccess) return e;
+  }
+  if (p.flags & PASS_PLANE) {  // one kernel, no variants; PDL as between the non-tile variants
+    if (c->prev_tile) a.pdl = 0;
+    c->prev_tile = false;
+    c->launches += 1;
+    return launch_axis_pass_plane(L, (int)c->nv[2], a, ntiles, c->stream);
   }
   const long long stride = a.stride;
   const int which = p.SV == 1 ? 0 : 1;
@@ -518,9 +542,15 @@ void t_action(const dso_ctx* c, std::vector<Pass>& out, bool standalone_f0, int 
 //   I0] ..; at step boundaries both kinetic coefficients' phases act in one
 //   pass per axis; the final kinetic action is [V F0 T0 I0] .. with the
 //   step's last coefficients.
+// With the plane pass (plane_active, D = 3) the passes of axes 1 and 2 are
+// one: [V F0 T0 I0] [F1 T1 I1 | F2 T2 I2].
 void t_action_axes(const dso_ctx* c, std::vector<Pass>& out, int u1, int u2, int tb, int tb2) {
   const int f = PASS_FWD | PASS_T | PASS_TAX;
   out.push_back(mkpass(0, u1 >= 0 ? c->S : 1, f, u1, u2, tb, tb2));
+  if (plane_active(c)) {  // [F1 T1 I1 | F2 T2 I2]: the plane pass
+    out.push_back(mkpass(1, 1, f | PASS_PLANE, -1, -1, tb, tb2));
+    return;
+  }
   for (int d = 1; d < c->Dv; ++d) out.push_back(mkpass(d, 1, f, -1, -1, tb, tb2));
 }
 
@@ -719,24 +749,27 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 // stream of jobs of one shape (a serving loop) tunes once.
 // The key holds everything that fixes the pass kinds and their lines: the
 // grid, S (which with the pass limits fixes the virtual axes), the batch,
-// precision, elementary method, device and the form of the kinetic step.
-using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int>;
+// precision, elementary method, device, the form of the kinetic step and the
+// plane-pass mode.
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int, int>;
 struct TuneVal {
   int G[DSO_MAX_VAXES][2];
   int variant[DSO_MAX_VAXES][2];
   int cps[DSO_MAX_VAXES][2];
+  int plane;  // plane pass chosen
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
 
 TuneKey tune_key(const dso_ctx* c) {
   return TuneKey(c->D, c->n[0], c->n[1], c->n[2], c->S, c->B, c->prec, c->elementary, c->device, c->max_line,
-                 c->max_tile, kin_axes(c) ? 1 : 0);
+                 c->max_tile, kin_axes(c) ? 1 : 0, c->plane_mode);
 }
 
 dso_status autotune_tiles(dso_ctx* c) {
   if (c->tuned) return DSO_OK;
   NvtxRange nvtx("dso_autotune");
+  c->plane_on = c->plane_mode == DSO_PLANE_ON;  // DSO_PLANE_AUTO: chosen below by timing
   // a fixed configuration (DSO_PLAN, as written by dso_tuned_plan)
   if (const char* plan = getenv("DSO_PLAN")) {
     const char* q = plan;
@@ -762,6 +795,8 @@ dso_status autotune_tiles(dso_ctx* c) {
       c->variant[d][w] = v;
       c->cps[d][w] = cp < 0 ? 0 : cp;
     }
+    // a trailing "plane;" selects the plane pass (unless DSO_PLANE_OFF)
+    if (std::strncmp(q, "plane;", 6) == 0) c->plane_on = true;
     c->tuned = true;
     return DSO_OK;
   }
@@ -772,6 +807,7 @@ dso_status autotune_tiles(dso_ctx* c) {
       std::memcpy(c->G, it->second.G, sizeof(c->G));
       std::memcpy(c->variant, it->second.variant, sizeof(c->variant));
       std::memcpy(c->cps, it->second.cps, sizeof(c->cps));
+      c->plane_on = it->second.plane != 0;
       c->tuned = true;
       return DSO_OK;
     }
@@ -801,12 +837,13 @@ dso_status autotune_tiles(dso_ctx* c) {
   for (const Pass& q : plan)
     if (q.u1 >= 0 && q.tb >= 0) both[q.axis][q.SV == 1 ? 0 : 1] = true;
   for (const Pass& q : plan) {
+    if (q.flags & PASS_PLANE) continue;  // one kernel: nothing to tune
     bool seen = false;
     for (const Pass& r : reps)
       if (r.axis == q.axis && (r.SV == 1) == (q.SV == 1)) seen = true;
     if (!seen) reps.push_back(q);
   }
-  TuneVal alt[2];  // whole-step candidates: tile kernel everywhere; the other variants where they apply
+  TuneVal alt[2] = {};  // whole-step candidates: tile kernel everywhere; the other variants where they apply
   std::memcpy(alt[0].G, c->G, sizeof(c->G));
   std::memcpy(alt[0].variant, c->variant, sizeof(c->variant));
   std::memcpy(alt[0].cps, c->cps, sizeof(c->cps));
@@ -905,7 +942,7 @@ dso_status autotune_tiles(dso_ctx* c) {
   // other variants wherever one applies -- are timed over host-launched
   // middle steps, and the fastest is kept.
   if (err == cudaSuccess && !getenv("DSO_VARIANT")) {
-    TuneVal cand[3];
+    TuneVal cand[3] = {};
     std::memcpy(cand[0].G, c->G, sizeof(c->G));
     std::memcpy(cand[0].variant, c->variant, sizeof(c->variant));
     std::memcpy(cand[0].cps, c->cps, sizeof(c->cps));
@@ -943,6 +980,30 @@ dso_status autotune_tiles(dso_ctx* c) {
     std::memcpy(c->G, cand[pick].G, sizeof(c->G));
     std::memcpy(c->variant, cand[pick].variant, sizeof(c->variant));
     std::memcpy(c->cps, cand[pick].cps, sizeof(c->cps));
+    // DSO_PLANE_AUTO: the chosen plan's middle step once more with the plane
+    // pass in place of the passes of axes 1 and 2
+    if (err == cudaSuccess && c->plane_mode == DSO_PLANE_AUTO && !c->plane_on) {
+      c->plane_on = true;
+      if (plane_active(c)) {
+        const std::vector<Pass> mid2 = step_passes(c, false);
+        for (const Pass& p : mid2)  // warm-up
+          if (err == cudaSuccess) err = run_pass(c, p);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3; ++r)
+          for (const Pass& p : mid2)
+            if (err == cudaSuccess) err = run_pass(c, p);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        const char* vb = getenv("DSO_TUNE_VERBOSE");
+        if (vb && vb[0] == '1' && err == cudaSuccess)
+          fprintf(stderr, "dso autotune: with the plane pass: %.2f us per middle step\n", ms * 1000.f / 3.f);
+        c->plane_on = err == cudaSuccess && ms < bestStep;
+      } else {
+        c->plane_on = false;
+      }
+    }
   }
   c->psi = keep;
   c->launches = launches + (c->launches - launches);
@@ -952,10 +1013,11 @@ dso_status autotune_tiles(dso_ctx* c) {
   c->tuned = true;
   if (!getenv("DSO_VARIANT")) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    TuneVal v;
+    TuneVal v = {};
     std::memcpy(v.G, c->G, sizeof(v.G));
     std::memcpy(v.variant, c->variant, sizeof(v.variant));
     std::memcpy(v.cps, c->cps, sizeof(v.cps));
+    v.plane = c->plane_on ? 1 : 0;
     g_tune_cache[tune_key(c)] = v;
   }
   return DSO_OK;
@@ -1923,6 +1985,7 @@ int dso_tuned_plan(const dso_ctx* c, char* out, int cap) {
       snprintf(e, sizeof(e), "%d,%d,%d,%d,%d;", d, w, c->variant[d][w], c->G[d][w], c->cps[d][w]);
       s += e;
     }
+  if (plane_active(c)) s += "plane;";
   if ((int)s.size() + 1 > cap) return fail(DSO_EINVAL, "dso_tuned_plan: buffer too small");
   std::memcpy(out, s.c_str(), s.size() + 1);
   return (int)s.size();
@@ -1948,6 +2011,19 @@ dso_status dso_set_kinetic_mode(dso_ctx* c, int mode) {
   drop_tables(c);
   c->kin_mode = mode;
   c->tuned = false;  // other pass kinds
+  return DSO_OK;
+}
+
+dso_status dso_set_plane_pass(dso_ctx* c, int mode) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (mode != DSO_PLANE_AUTO && mode != DSO_PLANE_OFF && mode != DSO_PLANE_ON)
+    return fail(DSO_EINVAL, "mode must be DSO_PLANE_AUTO, DSO_PLANE_OFF or DSO_PLANE_ON");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  c->plane_mode = mode;
+  c->plane_on = false;
+  c->tuned = false;  // other pass list
   return DSO_OK;
 }
 
@@ -2051,6 +2127,7 @@ int batch_G(const dso_ctx* c, int L, int SV) {
 dso_status batch_list(dso_ctx* c, const std::vector<Pass>& passes, std::vector<BatchPass>& out) {
   out.clear();
   for (const Pass& p : passes) {
+    if (p.flags & PASS_PLANE) return fail(DSO_EINVAL, "internal: the plane pass in a batch slot");
     BatchPass bp{};
     long long ntiles = 0;
     const cudaError_t e = build_pass_args(c, p, bp.a, ntiles);
@@ -2154,6 +2231,7 @@ dso_status dso_batch_add(dso_batch* b, dso_ctx* c, double t, double dt, int* slo
       c->variant[d][0] = c->variant[d][1] = 0;
     }
     c->tuned = true;  // the batch's tile layout, not the autotuner's
+    c->plane_on = false;  // line passes only
     drop_graph(c);
     st = batch_list(c, step_passes(c, true), s.first);
     if (st == DSO_OK) st = batch_list(c, step_passes(c, false), s.mid);

@@ -13,6 +13,8 @@ enum PassFlags : int {
                        // before the inverse FFT, twiddles after the forward FFT
   PASS_TAX = 16,       // with PASS_T: the phase of this axis alone, a table of L entries
                        // indexed by the momentum index along the line (separable kinetic step)
+  PASS_PLANE = 32,     // with PASS_T | PASS_TAX on axis D-2 of a 3-D grid: the pass also runs
+                       // [F T I] along axis D-1 (axis_pass_plane.cuh), one launch for both
 };
 
 // Complex arrays are double2 (FP64 path) or float2 (FP32 storage mode).
@@ -51,6 +53,7 @@ struct PassArgs {
   int xtw_n2_log2;         // log2 n2 (length of the second factor of the split axis)
   int xtw_s2_log2;         // log2 of the second factor's stride (product of the later axes)
   int wait_probe;          // > 0: TMA variant's bounded-wait diagnostics (polls of a barrier no copy completes)
+  const void* tw2;         // PASS_PLANE: twiddles of axis D-1, or null
 };
 
 // Tile index -> (first staged surface over all jobs, job).  A pass staging

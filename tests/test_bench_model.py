@@ -46,3 +46,17 @@ def test_kind_names(monkeypatch):
     assert bench.kind_name(_kind(2, 2 | 4, 1, 4)) == "axis_pass_reg_kernel<L=64,SV=1> [F2 T I2]"
     assert bench.kind_name(_kind(1, 2 | 4 | 16, 1, 4)) == "axis_pass_reg_kernel<L=64,SV=1> [F1 T1 I1]"
     assert bench.kind_name(_kind(0, 2 | 4 | 16 | 256, 3, 4)) == "axis_pass_reg_kernel<L=64,SV=3> [V F0 T0 I0]"
+
+
+def test_plane_pass_counts_both_axes(monkeypatch):
+    n, S = (128, 128, 128), 3
+    amps = S * 128 ** 3
+    f, b = bench.pass_flops_bytes(_kind(1, 2 | 4 | 16 | 32, surfaces=1, variant=0), n, S, 8)
+    f1, b1 = bench.pass_flops_bytes(_kind(1, 2 | 4 | 16, surfaces=1), n, S, 8)
+    f2, b2 = bench.pass_flops_bytes(_kind(2, 2 | 4 | 16, surfaces=1), n, S, 8)
+    assert f == f1 + f2                     # the two line passes' arithmetic
+    assert b == b1 + b2 - 2 * 8 * amps      # one psi round trip instead of two
+    monkeypatch.setattr(bench, "N_GRID", n)
+    monkeypatch.setitem(bench.W, "fp32", True)
+    assert bench.kind_name(_kind(1, 2 | 4 | 16 | 32, 1, 0)) == \
+        "axis_pass_plane_kernel<LA=128,LB=128,float2> [F1 T1 I1 F2 T2 I2]"
