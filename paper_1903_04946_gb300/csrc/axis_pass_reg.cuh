@@ -14,7 +14,8 @@
 // kinetic phase and the inverse FFT follow each other without any reordering.
 // Every butterfly is the tile kernel's -- the same radix plan (Plan<L>), the
 // same tangent-form twiddles and the same inputs in the same order -- so the
-// two kernels give bitwise the same results:
+// two kernels give bitwise the same results (for L = 128 up to the sign of a
+// zero: the butterflies with twiddle index 0 skip their exact unit factors):
 //   L =  32: radix 4 (butterflies j = t, t + 4) then radix 8 (j = t);
 //   L =  64: radix 8 (j = t) then radix 8 (j = t);
 //   L = 128: radix 2 (j = t + 8r), radix 8 (j = 2t, 2t + 1), then radix 8
@@ -159,6 +160,46 @@ __device__ __forceinline__ void dft8_tw_s(C* x, C w1, C w2, C w4, C w8, RealT<C>
   x[6] = y6;
 }
 
+// dft8_tw_s for butterfly k = 0, whose twiddles w1 = w2 = w4 = (1, 0)
+// exactly: with tangent 0 and cosine 1 each of their tangent pairs is the
+// sum and difference of its operands (or of a and -+i b), rounded once as
+// the FMAs round it, so only the w8 pairs keep the tangent form.  The
+// outputs are dft8_tw_s's up to the sign of a zero.
+template <typename C>
+__device__ __forceinline__ void pair_add(C& a, C& b) {
+  const C p = cadd(a, b), q = csub(a, b);
+  a = p;
+  b = q;
+}
+template <typename C>
+__device__ __forceinline__ void pair_rot(C& a, C& b, RealT<C> sg) {  // (a -+ i b, a +- i b)
+  const C p = mkc(fma(sg, b.y, a.x), fma(-sg, b.x, a.y));
+  const C q = mkc(fma(-sg, b.y, a.x), fma(sg, b.x, a.y));
+  a = p;
+  b = q;
+}
+template <typename C>
+__device__ __forceinline__ void dft8_k0_s(C* x, C w8, RealT<C> sg) {
+  const auto t8 = sg * w8.y, c8 = sg * w8.x;
+  pair_add(x[0], x[4]);
+  pair_add(x[2], x[6]);
+  pair_add(x[1], x[5]);
+  pair_add(x[3], x[7]);
+  pair_add(x[0], x[2]);
+  pair_rot(x[4], x[6], sg);
+  pair_add(x[1], x[3]);
+  pair_rot(x[5], x[7], sg);
+  pair_add(x[0], x[1]);
+  tan_pair_s<false>(x[4], x[5], w8.x, t8, c8);
+  pair_rot(x[2], x[3], sg);
+  tan_pair_s<true>(x[6], x[7], w8.x, t8, c8);
+  const C y1 = x[4], y4 = x[1], y3 = x[6], y6 = x[3];
+  x[1] = y1;
+  x[4] = y4;
+  x[3] = y3;
+  x[6] = y6;
+}
+
 // Inverse or forward FFT of SV lines (one per staged surface) at this
 // thread's line position.  The register stages of all SV lines share the
 // twiddle loads; the lines go through the one exchange buffer (G lines) in
@@ -189,9 +230,9 @@ __device__ __forceinline__ void fft_reg(C (&v)[SV][RegPlan<L>::VPT], C* ln, int 
 #pragma unroll
       for (int r = 0; r < 8; ++r) dft2<false>(v[s][r], v[s][r + 8]);  // stage 1: j = t + 8r -> y[2j], y[2j + 1]
     }
-    load_tw8<128>(tw, 0, w1, w2, w4, w8);  // stage 2 (Ls = 2): j = 2t (k = 0), inputs y[2t + 16r]
+    w8 = __ldg(&tw[128 / 8]);  // stage 2 (Ls = 2): j = 2t (k = 0), inputs y[2t + 16r]
 #pragma unroll
-    for (int s = 0; s < SV; ++s) dft8_tw_s(&v[s][0], w1, w2, w4, w8, sg);
+    for (int s = 0; s < SV; ++s) dft8_k0_s(&v[s][0], w8, sg);
     load_tw8<128>(tw, 8, w1, w2, w4, w8);  // j = 2t + 1 (k = 1), inputs y[2t + 1 + 16r]
 #pragma unroll
     for (int s = 0; s < SV; ++s) dft8_tw_s(&v[s][8], w1, w2, w4, w8, sg);

@@ -33,6 +33,8 @@ def _run(dso, problems, order, scheme, t, dt, mode, elementary="VTV", fp32=False
             ctx.load_batch(problems)
         dso.dso_set_scheme(ctx.ctx, order, dso.SCHEME_CODES[scheme], el)
         dso.dso_set_kinetic_mode(ctx.ctx, mode)
+        # one pass per axis: the plane pass (axes 1 and 2 in one launch) has its own tests
+        dso.dso_set_plane_pass(ctx.ctx, dso.DSO_PLANE_OFF)
         if limits:
             dso.dso_set_pass_limits(ctx.ctx, *limits)
         ctx.propagate(t, dt)
