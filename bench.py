@@ -201,19 +201,24 @@ def pass_flops_bytes(kind, n, S, esz=16):
     if f & 4:  # the kinetic phase: a grid-sized table, or (flag 16) one of this axis alone
         flops += 6 * amps
         bytes_ += esz * (L if f & 16 else P)
-    if f & 32:  # plane pass: the same forward FFT, phase and inverse FFT along the next axis too
+    if f & 32:  # plane pass: the forward and inverse FFT along the next axis too
         Lb = n[kind["axis"] + 1]
-        flops += 2 * (amps // Lb) * 5 * Lb * math.log2(Lb) + 6 * amps
-        bytes_ += esz * Lb
+        flops += 2 * (amps // Lb) * 5 * Lb * math.log2(Lb)
+        if f & 16:  # and that axis's own phase
+            flops += 6 * amps
+            bytes_ += esz * Lb
     return flops, bytes_
 
 
 def kind_name(k):
     f = k["flags"]
-    if f & 32:  # plane pass over axes d, d + 1
-        d = k["axis"]
-        return "axis_pass_plane_kernel<LA=%d,LB=%d%s> [F%d T%d I%d F%d T%d I%d]" % (
-            N_GRID[d], N_GRID[d + 1], ",float2" if W["fp32"] else "", d, d, d, d + 1, d + 1, d + 1)
+    if f & 32:  # plane pass over axes d, d + 1: per-axis phases, or the grid's phase
+        d, e = k["axis"], k["axis"] + 1
+        if f & 16:
+            return "axis_pass_plane_kernel<LA=%d,LB=%d%s> [F%d T%d I%d F%d T%d I%d]" % (
+                N_GRID[d], N_GRID[e], ",float2" if W["fp32"] else "", d, d, d, e, e, e)
+        return "axis_pass_plane_joint_kernel<LA=%d,LB=%d%s> [F%d F%d T I%d I%d]" % (
+            N_GRID[d], N_GRID[e], ",float2" if W["fp32"] else "", d, e, e, d)
     parts = []
     if f & 1:
         parts.append(f"I{k['axis']}")

@@ -381,18 +381,19 @@ dso_status dso_set_boundary_merge(dso_ctx* ctx, int merged);
  * is kept. */
 dso_status dso_set_kinetic_mode(dso_ctx* ctx, int mode);
 
-/* Plane pass of the per-axis kinetic step on 3-D grids.  The per-axis
- * kinetic step (dso_set_kinetic_mode) applies exp(-i dt p_d^2 / (2 m_d)) of
- * the two last axes d = 1, 2 in one pass each, one round trip of the
- * wavefunction through device memory per axis.  With the plane pass both
- * run in one: each n_1 x n_2 plane of one surface is held by one cluster of
- * CTAs, which transforms its columns, applies axis 1's phase and transforms
- * back, exchanges the plane through the CTAs' shared memory, and does the
- * same along its rows (two passes per substep instead of three).  The same
- * FFTs, phases and products in the same order: the result is bitwise that
- * of the two passes.  Applies to 3-D grids of whole axes (none split) with
- * n_1 and n_2 in {32, 64, 128} and the per-axis kinetic step; elsewhere, and
- * for jobs in a batch slot, the mode has no effect.  DSO_PLANE_ON uses it
+/* Plane pass of the kinetic step on 3-D grids.  The kinetic step's work on
+ * the two last axes d = 1, 2 takes one round trip of the wavefunction
+ * through device memory per pass: with the per-axis step (dso_set_kinetic_
+ * mode) [F1 T1 I1] [F2 T2 I2], with the joint step [F1] [F2 T I2] [I1].  The
+ * plane pass runs them in one launch: each n_1 x n_2 plane of one surface is
+ * held by one cluster of CTAs, which transforms its columns, exchanges the
+ * plane through the CTAs' shared memory and transforms its rows (per axis:
+ * each axis's phase between its own FFTs; joint: the grid's phase between
+ * the row FFTs, then a second exchange and the inverse column FFTs).  The
+ * same FFTs, phases and products in the same order: the result is bitwise
+ * that of the line passes.  Applies to 3-D grids of whole axes (none split)
+ * with n_1 and n_2 in {32, 64, 128}; elsewhere, and for jobs in a batch
+ * slot, the mode has no effect.  DSO_PLANE_ON uses it
  * wherever it applies; DSO_PLANE_OFF never; DSO_PLANE_AUTO (the default)
  * lets the autotuner time a middle step both ways and keep the faster (with
  * autotuning off, as DSO_PLANE_OFF).  Any other mode returns DSO_EINVAL.

@@ -153,4 +153,114 @@ __global__ void __launch_bounds__(128, sizeof(C) == 8 ? 5 : 4) axis_pass_plane_k
   }
 }
 
+// The joint kinetic step's passes over the same planes, [F_a | F_b T I_b |
+// I_a]: the forward FFT along a, then along b, the phase of the whole grid
+// (one entry per grid point, Sec. II G's joint form), the inverse FFT along
+// b and the inverse FFT along a -- the line passes [F_a] [F_b T I_b] [I_a]
+// in one launch.  As axis_pass_plane_kernel, with a second exchange: after
+// phase B each amplitude goes into the shared memory of the CTA that owns
+// its column (a column buffer, WB columns of LA + 1 elements), and phase C
+// transforms the columns back and stores them.  The row and column buffers
+// are separate, so no CTA writes where another may still read.
+template <int LA, int LB, typename C>
+struct PlaneJoint {
+  using PG = PlaneGeom<LA, LB, C>;
+  static constexpr int CS = LA + 1;            // column stride (odd: the strided reads are conflict-free)
+  static constexpr int CE = PG::WB * CS;       // column buffer (elements)
+};
+
+template <int LA, int LB, typename C>
+__host__ __device__ constexpr size_t plane_joint_smem_bytes() {
+  return (size_t)(PlaneGeom<LA, LB, C>::XE + PlaneGeom<LA, LB, C>::RE + PlaneJoint<LA, LB, C>::CE) * sizeof(C);
+}
+
+// a.tau (a.tau2) is the grid's phase table ([P] per unique coefficient, 1/P
+// folded in); a.tau2_scale is P.
+template <int LA, int LB, typename C>
+__global__ void __launch_bounds__(128, 4) axis_pass_plane_joint_kernel(PassArgs a) {
+  using PG = PlaneGeom<LA, LB, C>;
+  using PJ = PlaneJoint<LA, LB, C>;
+  constexpr int TPA = RegPlan<LA>::TPL, VA = RegPlan<LA>::VPT;
+  constexpr int TPB = RegPlan<LB>::TPL, VB = RegPlan<LB>::VPT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* X = reinterpret_cast<C*>(smraw);  // FFT exchange buffer
+  C* R = X + PG::XE;                   // this CTA's rows [WA][RS]
+  C* Q = R + PG::RE;                   // this CTA's columns [WB][CS]
+  const int tid = threadIdx.x;
+  const unsigned rank = cluster_rank();
+  cluster_arrive_relaxed();  // waited for before the first remote store
+  const long long plane = blockIdx.x / PG::K;
+  C* psi = reinterpret_cast<C*>(a.psi) + (size_t)plane * (LA * LB);
+  // the plane's first point in the grid-sized phase table (planes of every
+  // job and surface share the grid's table)
+  const long long tplane = (plane % (a.P / (LA * LB))) * (LA * LB);
+  const C* tw_a = reinterpret_cast<const C*>(a.tw);
+  const C* tw_b = reinterpret_cast<const C*>(a.tw2);
+  const unsigned rbase = (unsigned)__cvta_generic_to_shared(R);
+  const unsigned qbase = (unsigned)__cvta_generic_to_shared(Q);
+  // phase A: columns, forward FFT along a; each amplitude to its row's owner
+  {
+    const int g = tid % PG::GA, t = tid / PG::GA;
+    C* ln = X + g * RegLayout<LA, false>::LS;
+    pdl_wait();  // psi is the previous pass's output
+#pragma unroll 1
+    for (int it = 0; it < PG::NA; ++it) {
+      const int col = (int)rank * PG::WB + it * PG::GA + g;
+      C v[1][VA];
+#pragma unroll
+      for (int m = 0; m < VA; ++m) v[0][m] = psi[(t + TPA * m) * LB + col];
+      if (it == PG::NA - 1) pdl_trigger();
+      fft_reg<LA, 1, false>(v, ln, t, tw_a, (RealT<C>)1);
+      if (it == 0) cluster_wait();
+#pragma unroll
+      for (int m = 0; m < VA; ++m) {
+        const int row = t + TPA * m;
+        st_cluster(rbase + (unsigned)(((row % PG::WA) * PG::RS + col) * (int)sizeof(C)), (unsigned)(row / PG::WA),
+                   v[0][m]);
+      }
+    }
+  }
+  cluster_arrive_release();
+  cluster_wait();  // every row complete
+  // phase B: rows, forward FFT along b, the phase, inverse FFT along b; each
+  // amplitude to its column's owner
+  {
+    const int g = tid / TPB, t = tid % TPB;
+    C* ln = X + g * RegLayout<LB, true>::LS;
+#pragma unroll 1
+    for (int it = 0; it < PG::NB; ++it) {
+      const int r = it * PG::GB + g, row = (int)rank * PG::WA + r;
+      C v[1][VB];
+#pragma unroll
+      for (int m = 0; m < VB; ++m) v[0][m] = R[r * PG::RS + t + TPB * m];
+      fft_reg<LB, 1, true>(v, ln, t, tw_b, (RealT<C>)1);
+      kinetic_reg<LB, 1>(v, a, tplane + (long long)row * LB, 0, t);
+      fft_reg<LB, 1, true>(v, ln, t, tw_b, (RealT<C>)-1);
+#pragma unroll
+      for (int m = 0; m < VB; ++m) {
+        const int col = t + TPB * m;
+        st_cluster(qbase + (unsigned)(((col % PG::WB) * PJ::CS + row) * (int)sizeof(C)), (unsigned)(col / PG::WB),
+                   v[0][m]);
+      }
+    }
+  }
+  cluster_arrive_release();
+  cluster_wait();  // every column complete
+  // phase C: columns, inverse FFT along a, stored
+  {
+    const int g = tid % PG::GA, t = tid / PG::GA;
+    C* ln = X + g * RegLayout<LA, false>::LS;
+#pragma unroll 1
+    for (int it = 0; it < PG::NA; ++it) {
+      const int cl = it * PG::GA + g, col = (int)rank * PG::WB + cl;
+      C v[1][VA];
+#pragma unroll
+      for (int m = 0; m < VA; ++m) v[0][m] = Q[cl * PJ::CS + t + TPA * m];
+      fft_reg<LA, 1, false>(v, ln, t, tw_a, (RealT<C>)-1);
+#pragma unroll
+      for (int m = 0; m < VA; ++m) psi[(t + TPA * m) * LB + col] = v[0][m];
+    }
+  }
+}
+
 }  // namespace dso

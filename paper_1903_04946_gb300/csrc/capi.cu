@@ -208,11 +208,12 @@ int64_t axis_table_off(const dso_ctx* c, int d) {
   return n;
 }
 
-// The plane pass ([F1 T1 I1] and [F2 T2 I2] in one launch) applies to the
-// per-axis kinetic step of a 3-D grid of whole axes whose two last axes are
-// register-resident line lengths; plane_on is the tuned choice.
+// The plane pass (the kinetic passes of axes 1 and 2 in one launch: [F1 T1
+// I1 | F2 T2 I2] per axis, [F1 | F2 T I2 | I1] joint) applies to a 3-D grid of
+// whole axes whose two last axes are register-resident line lengths;
+// plane_on is the tuned choice.
 bool plane_supported(const dso_ctx* c) {
-  return kin_axes(c) && c->D == 3 && c->Dv == 3 && c->plane_mode != DSO_PLANE_OFF &&
+  return c->D == 3 && c->Dv == 3 && c->plane_mode != DSO_PLANE_OFF &&
          axis_pass_plane_supported((int)c->nv[1], (int)c->nv[2], c->prec == DSO_FP32);
 }
 
@@ -524,9 +525,15 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
 //   the next share one kinetic pass; final kinetic action then [I0].
 // TVT, D = 1:   [F0 T I0], then [V F0 T I0] per substep; the final pass is
 //   [V F0 T I0] with the step's last coefficients.
+// With the plane pass (plane_active, D = 3) [F1] [F2 T I2] [I1] is one pass,
+// [F1 | F2 T I2 | I1].
 void t_action(const dso_ctx* c, std::vector<Pass>& out, bool standalone_f0, int tb, int tb2) {
   const int D = c->Dv;
   if (standalone_f0) out.push_back(mkpass(0, 1, PASS_FWD));
+  if (plane_active(c)) {  // [F1 | F2 T I2 | I1]: the plane pass
+    out.push_back(mkpass(1, 1, PASS_FWD | PASS_T | PASS_PLANE, -1, -1, tb, tb2));
+    return;
+  }
   for (int d = 1; d <= D - 2; ++d) out.push_back(mkpass(d, 1, PASS_FWD));
   out.push_back(mkpass(D - 1, 1, PASS_FWD | PASS_T, -1, -1, tb, tb2));
   for (int d = D - 2; d >= 1; --d) out.push_back(mkpass(d, 1, PASS_INV_FIRST));

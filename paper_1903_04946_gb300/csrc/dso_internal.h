@@ -91,10 +91,11 @@ int axis_pass_reg_lines(int L, int SV);
 // the register-resident variant takes lines of L points along an axis of
 // `stride` with SV surfaces staged (dec0: surface 0 decoupled)
 bool axis_pass_reg_supported(int L, int SV, bool fp32, long long stride, bool dec0);
-// Plane pass (axis_pass_plane.cuh): [F T I] along axis D-2 (LA points,
-// stride LB) then along axis D-1 (LB points) of a 3-D grid, one cluster of
-// CTAs per LA x LB plane of one surface; `args` is the axis D-2 pass's with
-// PASS_PLANE and tw2 the twiddles of LB points.
+// Plane pass (axis_pass_plane.cuh) over axes D-2 (LA points, stride LB)
+// and D-1 (LB points) of a 3-D grid, one cluster of CTAs per LA x LB plane of
+// one surface: with PASS_TAX [F T I] along each axis in turn (per-axis
+// phases), without it [F_a | F_b T I_b | I_a] (the grid's phase); `args` is
+// the axis D-2 pass's with PASS_PLANE and tw2 the twiddles of LB points.
 bool axis_pass_plane_supported(int LA, int LB, bool fp32);
 cudaError_t launch_axis_pass_plane(int LA, int LB, const PassArgs& args, long long nplanes, cudaStream_t st);
 // per-SV launchers (one translation unit each)

@@ -13,8 +13,9 @@ enum PassFlags : int {
                        // before the inverse FFT, twiddles after the forward FFT
   PASS_TAX = 16,       // with PASS_T: the phase of this axis alone, a table of L entries
                        // indexed by the momentum index along the line (separable kinetic step)
-  PASS_PLANE = 32,     // with PASS_T | PASS_TAX on axis D-2 of a 3-D grid: the pass also runs
-                       // [F T I] along axis D-1 (axis_pass_plane.cuh), one launch for both
+  PASS_PLANE = 32,     // with PASS_FWD | PASS_T on axis D-2 of a 3-D grid, one launch for the
+                       // planes of axes D-2 and D-1 (axis_pass_plane.cuh): with PASS_TAX
+                       // [F T I] along each axis in turn; without, [F_a | F_b T I_b | I_a]
 };
 
 // Complex arrays are double2 (FP64 path) or float2 (FP32 storage mode).

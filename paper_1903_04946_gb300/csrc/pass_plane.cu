@@ -1,5 +1,6 @@
-// pass_plane.cu -- instantiation and launch of the plane pass
-// (axis_pass_plane.cuh): planes of LA x LB points, LA, LB in {32, 64, 128}.
+// pass_plane.cu -- instantiation and launch of the plane passes
+// (axis_pass_plane.cuh) of the per-axis and the joint kinetic step: planes of
+// LA x LB points, LA, LB in {32, 64, 128}.
 #include "axis_pass_plane.cuh"
 #include "dso_internal.h"
 
@@ -12,16 +13,19 @@ cudaError_t launch_plane_t(const PassArgs& a, long long nplanes, cudaStream_t st
     return cudaErrorInvalidConfiguration;
   } else {
     using PG = PlaneGeom<LA, LB, C>;
-    constexpr size_t smem = plane_smem_bytes<LA, LB, C>();
-    static_assert(smem <= 227 * 1024, "plane pass shared memory");
-    static bool attr_set[64] = {};
+    // per-axis phases (PASS_TAX): one exchange; the grid's phase: two
+    const bool axes = (a.flags & PASS_TAX) != 0;
+    constexpr size_t smem_axes = plane_smem_bytes<LA, LB, C>(), smem_joint = plane_joint_smem_bytes<LA, LB, C>();
+    static_assert(smem_axes <= 227 * 1024 && smem_joint <= 227 * 1024, "plane pass shared memory");
+    const size_t smem = axes ? smem_axes : smem_joint;
+    static bool attr_set[2][64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    void (*k)(PassArgs) = axis_pass_plane_kernel<LA, LB, C>;
-    if (!attr_set[dev]) {
+    void (*k)(PassArgs) = axes ? axis_pass_plane_kernel<LA, LB, C> : axis_pass_plane_joint_kernel<LA, LB, C>;
+    if (!attr_set[axes][dev]) {
       const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      attr_set[dev] = true;
+      attr_set[axes][dev] = true;
     }
     const long long ctas = nplanes * PG::K;
     if (nplanes < 1 || ctas > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -75,7 +79,7 @@ bool axis_pass_plane_supported(int LA, int LB, bool fp32) {
 }
 
 cudaError_t launch_axis_pass_plane(int LA, int LB, const PassArgs& a, long long nplanes, cudaStream_t st) {
-  const int need = PASS_FWD | PASS_T | PASS_TAX | PASS_PLANE;
+  const int need = PASS_FWD | PASS_T | PASS_PLANE;  // with or without PASS_TAX
   if ((a.flags & need) != need || (a.flags & (PASS_INV_FIRST | PASS_XTW)) || a.U1 || a.U2 || !a.tau || !a.tw ||
       !a.tw2 || a.stride != LB || !axis_pass_plane_supported(LA, LB, a.fp32 != 0) ||
       nplanes * LA * LB != (long long)a.nbatch * a.S * a.P)

@@ -60,3 +60,17 @@ def test_plane_pass_counts_both_axes(monkeypatch):
     monkeypatch.setitem(bench.W, "fp32", True)
     assert bench.kind_name(_kind(1, 2 | 4 | 16 | 32, 1, 0)) == \
         "axis_pass_plane_kernel<LA=128,LB=128,float2> [F1 T1 I1 F2 T2 I2]"
+
+
+def test_joint_plane_pass_counts_three_line_passes(monkeypatch):
+    n, S = (64, 64, 64), 3
+    amps = S * 64 ** 3
+    f, b = bench.pass_flops_bytes(_kind(1, 2 | 4 | 32, surfaces=1), n, S, 16)
+    parts = [bench.pass_flops_bytes(_kind(1, 2, surfaces=1), n, S, 16),
+             bench.pass_flops_bytes(_kind(2, 2 | 4, surfaces=1), n, S, 16),
+             bench.pass_flops_bytes(_kind(1, 1, surfaces=1), n, S, 16)]
+    assert f == sum(p[0] for p in parts)
+    assert b == sum(p[1] for p in parts) - 4 * 16 * amps  # one psi round trip instead of three
+    monkeypatch.setattr(bench, "N_GRID", n)
+    monkeypatch.setitem(bench.W, "fp32", False)
+    assert bench.kind_name(_kind(1, 2 | 4 | 32, 1, 0)) == "axis_pass_plane_joint_kernel<LA=64,LB=64> [F1 F2 T I2 I1]"
