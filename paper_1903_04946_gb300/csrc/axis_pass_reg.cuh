@@ -506,17 +506,21 @@ __global__ void __launch_bounds__(reg_threads<SV>(), SV == 1 ? 4 : 2) axis_pass_
 
 // Passes that stage all S > 2 surfaces with surface 0 decoupled (dec0: the
 // unitary is block diagonal, U_00 and the S-1 x S-1 block of the others):
-// every tile is two CTAs, the even one transforming surface 0 with the
-// diagonal entry U_00 (packed entry 0), the odd one surfaces 1..S-1 with the
-// block (packed entries S .. S(S+1)/2 - 1, in the packed order of an S-1
-// matrix).  The products are those of matvec_sym with dec0, bit for bit, and
-// each CTA holds the amplitudes of fewer surfaces, so more CTAs share an SM.
+// every tile is two CTAs, one transforming surface 0 with the diagonal entry
+// U_00 (packed entry 0), one surfaces 1..S-1 with the block (packed entries
+// S .. S(S+1)/2 - 1, in the packed order of an S-1 matrix).  The products are
+// those of matvec_sym with dec0, bit for bit, and each CTA holds the
+// amplitudes of fewer surfaces, so more CTAs share an SM.  The first half of
+// the grid takes the blocks (the longer CTAs, started first), the second half
+// surface 0, so that an SM mostly runs one role's code at a time.
 template <int L, int S, bool CONTIG, typename C>
 __global__ void __launch_bounds__(reg_threads<S>(), 3) axis_pass_reg_split_kernel(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const TileJob tj = split_tile(blockIdx.x >> 1, S, a);
+  const unsigned half = gridDim.x >> 1;
+  const bool block = blockIdx.x < half;
+  const TileJob tj = split_tile(block ? blockIdx.x : blockIdx.x - half, S, a);
   C* sm = reinterpret_cast<C*>(smraw);
-  if ((blockIdx.x & 1) == 0)
+  if (!block)
     reg_tile<L, 1, CONTIG>(a, tj, 0, 0, 0, a.U1 != nullptr, sm);
   else
     reg_tile<L, S - 1, CONTIG>(a, tj, 1, S, 0, a.U1 != nullptr, sm);
