@@ -851,6 +851,12 @@ dso_status autotune_tiles(dso_ctx* c) {
     if (!seen) reps.push_back(q);
   }
   TuneVal alt[2] = {};  // whole-step candidates: tile kernel everywhere; the other variants where they apply
+  // fastest time alone, and its tile lines and CTAs per SM, of every variant of every kind
+  float vbest[DSO_MAX_VAXES][2][5];
+  int vG[DSO_MAX_VAXES][2][5] = {}, vC[DSO_MAX_VAXES][2][5] = {};
+  for (auto& x : vbest)
+    for (auto& y : x)
+      for (float& z : y) z = 1e30f;
   std::memcpy(alt[0].G, c->G, sizeof(c->G));
   std::memcpy(alt[0].variant, c->variant, sizeof(c->variant));
   std::memcpy(alt[0].cps, c->cps, sizeof(c->cps));
@@ -911,6 +917,11 @@ dso_status autotune_tiles(dso_ctx* c) {
               bestV = var;
               bestC = c->cps[d][which];
             }
+            if (err == cudaSuccess && ms < vbest[d][which][var]) {
+              vbest[d][which][var] = ms;
+              vG[d][which][var] = (int)G;
+              vC[d][which][var] = c->cps[d][which];
+            }
             if (err == cudaSuccess && var == 0 && ms < best0) {
               best0 = ms;
               bestG0 = (int)G;
@@ -944,11 +955,29 @@ dso_status autotune_tiles(dso_ctx* c) {
   // inside the step depends on its neighbours (programmatic dependent launch
   // overlaps the tail of one pass of the persistent, TMA or
   // register-resident variants with the start of the next, and is not used
-  // next to the tile kernel).  So three candidate plans -- the fastest
-  // variant of every kind, the tile kernel everywhere, and the fastest of the
-  // other variants wherever one applies -- are timed over host-launched
-  // middle steps, and the fastest is kept.
+  // next to the tile kernel; tables that stay in L2 across repeated
+  // launches of one pass are evicted by the others).  So three candidate
+  // plans -- the fastest variant of every kind, the tile kernel everywhere,
+  // and the fastest of the other variants wherever one applies -- are timed
+  // over host-launched middle steps, and the fastest is kept; then each kind,
+  // in turn, tries its other variants that timed within 1.3x of its fastest
+  // alone, kept where the whole middle step gets faster; then the plane pass.
   if (err == cudaSuccess && !getenv("DSO_VARIANT")) {
+    const char* vb = getenv("DSO_TUNE_VERBOSE");
+    const bool verbose = vb && vb[0] == '1';
+    auto time_mid = [&](const std::vector<Pass>& mid, float& ms) {
+      for (const Pass& p : mid)  // warm-up
+        if (err == cudaSuccess) err = run_pass(c, p);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3; ++r)
+        for (const Pass& p : mid)
+          if (err == cudaSuccess) err = run_pass(c, p);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      return err == cudaSuccess;
+    };
     TuneVal cand[3] = {};
     std::memcpy(cand[0].G, c->G, sizeof(c->G));
     std::memcpy(cand[0].variant, c->variant, sizeof(c->variant));
@@ -966,20 +995,10 @@ dso_status autotune_tiles(dso_ctx* c) {
       std::memcpy(c->G, cand[k].G, sizeof(c->G));
       std::memcpy(c->variant, cand[k].variant, sizeof(c->variant));
       std::memcpy(c->cps, cand[k].cps, sizeof(c->cps));
-      for (const Pass& p : mid)  // warm-up
-        if (err == cudaSuccess) err = run_pass(c, p);
-      if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-      for (int r = 0; r < 3; ++r)
-        for (const Pass& p : mid)
-          if (err == cudaSuccess) err = run_pass(c, p);
-      if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.f;
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-      const char* vb = getenv("DSO_TUNE_VERBOSE");
-      if (vb && vb[0] == '1' && err == cudaSuccess)
-        fprintf(stderr, "dso autotune: whole-step candidate %d: %.2f us per middle step\n", k, ms * 1000.f / 3.f);
-      if (err == cudaSuccess && ms < bestStep) {
+      if (!time_mid(mid, ms)) break;
+      if (verbose) fprintf(stderr, "dso autotune: whole-step candidate %d: %.2f us per middle step\n", k, ms * 1000.f / 3.f);
+      if (ms < bestStep) {
         bestStep = ms;
         pick = k;
       }
@@ -987,26 +1006,45 @@ dso_status autotune_tiles(dso_ctx* c) {
     std::memcpy(c->G, cand[pick].G, sizeof(c->G));
     std::memcpy(c->variant, cand[pick].variant, sizeof(c->variant));
     std::memcpy(c->cps, cand[pick].cps, sizeof(c->cps));
+    // coordinate descent over the kinds of the middle step
+    std::vector<std::pair<int, int>> kinds;
+    for (const Pass& p : mid) {
+      const std::pair<int, int> k(p.axis, p.SV == 1 ? 0 : 1);
+      if (!(p.flags & PASS_PLANE) && std::find(kinds.begin(), kinds.end(), k) == kinds.end()) kinds.push_back(k);
+    }
+    for (const auto& k : kinds) {
+      const int d = k.first, w = k.second;
+      float kbest = 1e30f;
+      for (int v = 0; v < 5; ++v) kbest = std::min(kbest, vbest[d][w][v]);
+      for (int v = 0; v < 5 && err == cudaSuccess; ++v) {
+        if (v == c->variant[d][w] || vbest[d][w][v] >= 1e30f || vbest[d][w][v] > 1.3f * kbest) continue;
+        const int g0 = c->G[d][w], v0 = c->variant[d][w], c0 = c->cps[d][w];
+        c->G[d][w] = vG[d][w][v];
+        c->variant[d][w] = v;
+        c->cps[d][w] = vC[d][w][v];
+        float ms = 0.f;
+        if (!time_mid(mid, ms)) break;
+        if (verbose)
+          fprintf(stderr, "dso autotune: axis %d SV %s on variant %d: %.2f us per middle step\n", d,
+                  w ? "S" : "1", v, ms * 1000.f / 3.f);
+        if (ms < bestStep) {
+          bestStep = ms;
+        } else {
+          c->G[d][w] = g0;
+          c->variant[d][w] = v0;
+          c->cps[d][w] = c0;
+        }
+      }
+    }
     // DSO_PLANE_AUTO: the chosen plan's middle step once more with the plane
     // pass in place of the passes of axes 1 and 2
     if (err == cudaSuccess && c->plane_mode == DSO_PLANE_AUTO && !c->plane_on) {
       c->plane_on = true;
       if (plane_active(c)) {
-        const std::vector<Pass> mid2 = step_passes(c, false);
-        for (const Pass& p : mid2)  // warm-up
-          if (err == cudaSuccess) err = run_pass(c, p);
-        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3; ++r)
-          for (const Pass& p : mid2)
-            if (err == cudaSuccess) err = run_pass(c, p);
-        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
         float ms = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-        const char* vb = getenv("DSO_TUNE_VERBOSE");
-        if (vb && vb[0] == '1' && err == cudaSuccess)
-          fprintf(stderr, "dso autotune: with the plane pass: %.2f us per middle step\n", ms * 1000.f / 3.f);
-        c->plane_on = err == cudaSuccess && ms < bestStep;
+        const bool ok = time_mid(step_passes(c, false), ms);
+        if (verbose && ok) fprintf(stderr, "dso autotune: with the plane pass: %.2f us per middle step\n", ms * 1000.f / 3.f);
+        c->plane_on = ok && ms < bestStep;
       } else {
         c->plane_on = false;
       }
