@@ -835,9 +835,12 @@ dso_status autotune_tiles(dso_ctx* c) {
   c->psi = c->work;
   const int64_t launches = c->launches;
   // every kind of pass (axis, surfaces staged) the propagation uses, with a
-  // representative pass of that kind
-  std::vector<Pass> plan = step_passes(c, true);
-  for (const Pass& q : step_passes(c, false)) plan.push_back(q);
+  // representative pass of that kind: from a middle step where the kind
+  // occurs there (the passes every later step repeats, e.g. [I0 V F0] rather
+  // than the first step's [V F0]), else from the first step or the final
+  // passes
+  std::vector<Pass> plan = step_passes(c, false);
+  for (const Pass& q : step_passes(c, true)) plan.push_back(q);
   for (const Pass& q : final_passes(c)) plan.push_back(q);
   std::vector<Pass> reps;
   bool both[DSO_MAX_VAXES][2] = {};  // some pass of the kind applies a potential and a kinetic phase (1-D)
