@@ -145,3 +145,10 @@ def test_library_optimal_coefficients_match_oracle(lib, order):
     assert list(ia) == sp.Ia and list(ib) == sp.Ib
     with pytest.raises(dso.DSOError):
         dso.dso_scheme_coefficients(4, dso.DSO_OPTIMAL)
+
+
+@pytest.mark.parametrize("name,arg", [("dso_set_plane_pass", 1), ("dso_set_kinetic_mode", 1),
+                                      ("dso_set_boundary_merge", 1)])
+def test_mode_setters_reject_a_null_context(lib, name, arg):
+    """The mode setters check their context before touching a device."""
+    assert getattr(lib, name)(None, arg) == dso.DSO_EINVAL
