@@ -66,6 +66,8 @@ enum { DSO_VTV = 0, DSO_TVT = 1, DSO_VT = 2, DSO_TV = 3 };
 enum { DSO_KINETIC_AUTO = -1, DSO_KINETIC_JOINT = 0, DSO_KINETIC_AXES = 1 };
 /* Plane pass (dso_set_plane_pass). */
 enum { DSO_PLANE_AUTO = -1, DSO_PLANE_OFF = 0, DSO_PLANE_ON = 1 };
+/* Potential operators (dso_set_operator_mode). */
+enum { DSO_OPERATORS_AUTO = -1, DSO_OPERATORS_TABLES = 0, DSO_OPERATORS_ON_THE_FLY = 1 };
 
 /* Limits of this build. */
 #define DSO_MAX_DIM 3
@@ -399,6 +401,32 @@ dso_status dso_set_kinetic_mode(dso_ctx* ctx, int mode);
  * autotuning off, as DSO_PLANE_OFF).  Any other mode returns DSO_EINVAL.
  * Drops the context's tuning; the state and tables are kept. */
 dso_status dso_set_plane_pass(dso_ctx* ctx, int mode);
+
+/* Potential operators precomputed or built per action (Sec. II F's
+ * memory/time trade-off).  DSO_OPERATORS_TABLES precomputes U_a(q) =
+ * exp(-i a dt V(q)) for every unique potential coefficient a (S(S+1)/2
+ * complex entries per grid point and coefficient, per job).
+ * DSO_OPERATORS_ON_THE_FLY stores, per grid point, only the part of U that
+ * does not depend on the coefficient -- for S = 2 the mean, half difference
+ * and coupling of V and its rotation rate (4 doubles), for S >= 3 the
+ * eigenvectors and eigenvalues of V (S^2 + S doubles) -- and assembles the
+ * table of each potential action into one of two slots right before the
+ * pass that applies it: one more kernel per action, table memory
+ * independent of the number of unique coefficients, and bitwise the same
+ * propagation.  DSO_OPERATORS_AUTO (the default) precomputes the tables when
+ * they take at most half the device memory free when the tables are built,
+ * and builds per action otherwise.  The kinetic tables are always
+ * precomputed (one phase per grid point, or per axis point, per coefficient).
+ * Jobs in a batch slot always use precomputed tables
+ * (DSO_OPERATORS_ON_THE_FLY makes dso_batch_add return DSO_EINVAL).  Any
+ * other mode returns DSO_EINVAL.  Drops the context's tables and tuning; the
+ * state is kept. */
+dso_status dso_set_operator_mode(dso_ctx* ctx, int mode);
+
+/* 1 when the context's current tables build the potential operators per
+ * action, 0 when they are precomputed (or not built yet); DSO_EINVAL for a
+ * null context. */
+int dso_operators_on_the_fly(const dso_ctx* ctx);
 
 /* Batch slots (continuous batching).  A batch advances many jobs -- each a
  * context with its own grid, surfaces, masses, potential, scheme and state,

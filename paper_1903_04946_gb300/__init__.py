@@ -24,6 +24,7 @@ SCHEME_CODES = {"triple_jump": DSO_TRIPLE_JUMP, "suzuki": DSO_SUZUKI, "optimal":
 DSO_VTV, DSO_TVT, DSO_VT, DSO_TV = 0, 1, 2, 3
 DSO_KINETIC_AUTO, DSO_KINETIC_JOINT, DSO_KINETIC_AXES = -1, 0, 1
 DSO_PLANE_AUTO, DSO_PLANE_OFF, DSO_PLANE_ON = -1, 0, 1
+DSO_OPERATORS_AUTO, DSO_OPERATORS_TABLES, DSO_OPERATORS_ON_THE_FLY = -1, 0, 1
 
 EXPORTS = (
     "dso_create", "dso_destroy", "dso_set_grid", "dso_set_batch", "dso_set_masses", "dso_load_potential",
@@ -34,7 +35,8 @@ EXPORTS = (
     "dso_phase_at_density_maximum", "dso_set_wait_probe", "dso_psi_device_pointer", "dso_set_pass_limits",
     "dso_batch_create", "dso_batch_destroy", "dso_batch_add", "dso_batch_step", "dso_batch_sync",
     "dso_batch_slot_status", "dso_batch_retire", "dso_batch_launch_count", "dso_batch_busy",
-    "dso_set_kinetic_mode", "dso_set_boundary_merge", "dso_set_plane_pass",
+    "dso_set_kinetic_mode", "dso_set_boundary_merge", "dso_set_plane_pass", "dso_set_operator_mode",
+    "dso_operators_on_the_fly",
 )
 
 _lib = None
@@ -88,6 +90,8 @@ def load(path: str = LIB):
         "dso_set_kinetic_mode": (i32, [vp, i32]),
         "dso_set_boundary_merge": (i32, [vp, i32]),
         "dso_set_plane_pass": (i32, [vp, i32]),
+        "dso_set_operator_mode": (i32, [vp, i32]),
+        "dso_operators_on_the_fly": (i32, [vp]),
         "dso_batch_create": (i32, [ctypes.POINTER(vp), i32, i32, vp]),
         "dso_batch_destroy": (None, [vp]),
         "dso_batch_add": (i32, [vp, vp, dbl, dbl, ctypes.POINTER(i32)]),
@@ -334,6 +338,16 @@ def dso_set_boundary_merge(ctx, merged):
 
 def dso_set_plane_pass(ctx, mode):
     _check(load().dso_set_plane_pass(ctx, int(mode)), "dso_set_plane_pass")
+
+
+def dso_set_operator_mode(ctx, mode):
+    _check(load().dso_set_operator_mode(ctx, int(mode)), "dso_set_operator_mode")
+
+
+def dso_operators_on_the_fly(ctx) -> bool:
+    r = load().dso_operators_on_the_fly(ctx)
+    _check(min(r, 0), "dso_operators_on_the_fly")
+    return r == 1
 
 
 def dso_batch_create(device: int = 0, precision: int = DSO_FP64, stream=None):

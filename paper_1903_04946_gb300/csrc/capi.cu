@@ -137,6 +137,9 @@ struct dso_ctx {
   int kin_mode = DSO_KINETIC_AUTO;  // dso_set_kinetic_mode
   int boundary_merged = 1;          // dso_set_boundary_merge: one table for a~_last + a~_0
   int plane_mode = DSO_PLANE_AUTO;  // dso_set_plane_pass
+  int op_mode = DSO_OPERATORS_AUTO;  // dso_set_operator_mode
+  bool otf = false;                  // potential operators built per action (tables_valid: in use)
+  double* eig = nullptr;             // otf: [B][eig_cache_doubles(S)][P], the coefficient-free part of U
   bool plane_on = false;            // the plan uses the plane pass (set by the autotuner)
   double* tau_a = nullptr;   // [na] potential coefficient * dt
   int n_vtab = 0, n_ttab = 0;  // numbers of potential and kinetic tables
@@ -254,10 +257,16 @@ void drop_graph(dso_ctx* c) {
 void drop_tables(dso_ctx* c) {
   drop_graph(c);
   dfree(c->Utab);
+  dfree(c->eig);
   dfree(c->tau);
   dfree(c->tau_a);
   c->tables_valid = false;
+  c->otf = false;
 }
+
+// Potential table slots per job: one per unique coefficient, or (operators
+// built per action) two, the pass's first and second table.
+int vslots(const dso_ctx* c) { return c->otf ? 2 : c->n_vtab; }
 
 void drop_model(dso_ctx* c) {
   drop_tables(c);
@@ -395,8 +404,11 @@ cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& n
   const size_t es = c->esz();
   a.psi = c->psi;
   const int NP = c->S * (c->S + 1) / 2;
-  a.U1 = p.u1 >= 0 ? at(c->Utab, (size_t)p.u1 * NP * c->P, es) : nullptr;
-  a.U2 = p.u2 >= 0 ? at(c->Utab, (size_t)p.u2 * NP * c->P, es) : nullptr;
+  // operators built per action: the pass reads slot 0 (first table) and
+  // slot 1 (second), which run_pass fills before launching it
+  const int s1 = c->otf ? (p.u1 >= 0 ? 0 : -1) : p.u1, s2 = c->otf ? (p.u2 >= 0 ? 1 : -1) : p.u2;
+  a.U1 = s1 >= 0 ? at(c->Utab, (size_t)s1 * NP * c->P, es) : nullptr;
+  a.U2 = s2 >= 0 ? at(c->Utab, (size_t)s2 * NP * c->P, es) : nullptr;
   a.fp32 = c->prec == DSO_FP32 ? 1 : 0;
   if (p.flags & PASS_TAX) {  // this axis's phase: [nb][sum_d n_d] tables, 1/L folded in
     const size_t len = (size_t)axis_table_len(c), off = (size_t)axis_table_off(c, p.axis);
@@ -431,15 +443,15 @@ cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& n
   if (a.G < 1 || (a.G & (a.G - 1)) || a.lines % a.G) return cudaErrorInvalidConfiguration;
   a.stride_log2 = ilog2(stride);
   a.G_log2 = ilog2(a.G);
-  a.ua = p.u1 >= 0 ? p.u1 : 0;
+  a.ua = s1 >= 0 ? s1 : 0;
   a.ub = p.tb >= 0 ? p.tb : 0;
   a.err = c->err;
   a.nbatch = c->B;
-  a.u_batch_stride = (long long)c->n_vtab * NP * c->P;
+  a.u_batch_stride = (long long)vslots(c) * NP * c->P;
   a.U_base = c->Utab;
   a.tau_base = c->tau;
   a.psi_elems = (long long)c->B * c->S * c->P;
-  a.u_elems = (long long)c->B * c->n_vtab * NP * c->P;
+  a.u_elems = (long long)c->B * vslots(c) * NP * c->P;
   a.tau_elems = (long long)c->n_ttab * (kin_axes(c) ? axis_table_len(c) : c->P);
   a.dec0 = c->dec0;
   a.ctas_per_sm = c->cps[p.axis][which];
@@ -455,12 +467,39 @@ cudaError_t build_pass_args(dso_ctx* c, const Pass& p, PassArgs& a, long long& n
   return cudaSuccess;
 }
 
+// Operators built per action: fill slot 0 (and 1) of every job with the
+// pass's potential table(s) from the stored coefficient-free part.  The
+// passes stage their tables before waiting for the previous kernel, so the
+// pass that follows is launched without programmatic dependent launch.
+cudaError_t build_operator_slots(dso_ctx* c, const Pass& p) {
+  const int NP = c->S * (c->S + 1) / 2;
+  const size_t nc = (size_t)eig_cache_doubles(c->S);
+  const int coef[2] = {p.u1, p.u2};
+  for (int k = 0; k < 2; ++k) {
+    if (coef[k] < 0) continue;
+    if (coef[k] >= c->n_vtab) return cudaErrorInvalidValue;
+    for (int b = 0; b < c->B; ++b) {
+      const cudaError_t e =
+          launch_unitary_from_cache(at(c->Utab, ((size_t)b * 2 + k) * NP * c->P, c->esz()), c->prec == DSO_FP32,
+                                    c->eig + (size_t)b * nc * c->P, c->tau_a + coef[k], c->S, c->P, c->stream);
+      if (e != cudaSuccess) return e;
+      c->launches += 1;
+    }
+  }
+  c->prev_tile = true;  // no programmatic dependent launch for the next pass
+  return cudaSuccess;
+}
+
 cudaError_t run_pass(dso_ctx* c, const Pass& p) {
   const int L = (int)c->nv[p.axis];
   PassArgs a;
   long long ntiles = 0;
   {
     const cudaError_t e = build_pass_args(c, p, a, ntiles);
+    if (e != cudaSuccess) return e;
+  }
+  if (c->otf && p.u1 >= 0) {
+    const cudaError_t e = build_operator_slots(c, p);
     if (e != cudaSuccess) return e;
   }
   if (p.flags & PASS_PLANE) {  // one kernel, no variants; PDL as between the non-tile variants
@@ -482,7 +521,7 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
     const int NP = c->S * (c->S + 1) / 2;
     bool ok = encode_view(&maps.psi, c->psi, c->P, L, stride, (long long)c->B * c->S, Wi, Go, p.SV);
     if (ok && p.u1 >= 0)
-      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)c->B * NP * (long long)c->n_vtab, Wi, Go,
+      ok = encode_view(&maps.tab, c->Utab, c->P, L, stride, (long long)c->B * NP * (long long)vslots(c), Wi, Go,
                        NP);
     if (ok && p.tb >= 0) {
       CUtensorMap* m = (p.u1 >= 0) ? &maps.tab2 : &maps.tab;
@@ -493,8 +532,8 @@ cudaError_t run_pass(dso_ctx* c, const Pass& p) {
     const long long t_per_set = a.lines / a.G;
     const long long i_last = ((t_per_set - 1) * a.G) % stride, o_last = ((t_per_set - 1) * a.G) / stride;
     if (i_last + Wi > stride || o_last + Go > outer) ok = false;
-    if (p.u1 >= 0 && ((long long)(c->B - 1) * c->n_vtab * NP + (long long)p.u1 * NP + NP >
-                      (long long)c->B * c->n_vtab * NP))
+    if (p.u1 >= 0 && ((long long)(c->B - 1) * vslots(c) * NP + (long long)a.ua * NP + NP >
+                      (long long)c->B * vslots(c) * NP))
       ok = false;
     if (p.tb >= 0 && p.tb >= c->n_ttab) ok = false;
     if (!ok) return cudaErrorInvalidConfiguration;
@@ -699,8 +738,12 @@ dso_status ensure_twiddles(dso_ctx* c) {
   return DSO_OK;
 }
 
-dso_status ensure_tables(dso_ctx* c, double dt) {
-  if (c->tables_valid && c->tables_dt == dt) return DSO_OK;
+// allow_otf = false (batch slots, whose work-list kernel reads tables only)
+// keeps the precomputed tables whatever the operator mode.
+dso_status ensure_tables(dso_ctx* c, double dt, bool allow_otf = true) {
+  if (!allow_otf && c->op_mode == DSO_OPERATORS_ON_THE_FLY)
+    return fail(DSO_EINVAL, "operators built per action (DSO_OPERATORS_ON_THE_FLY) are not available in a batch slot");
+  if (c->tables_valid && c->tables_dt == dt && (allow_otf || !c->otf)) return DSO_OK;
   NvtxRange nvtx("dso_tables");
   CK(cudaGetLastError());  // surface any error left pending by an earlier call
   drop_tables(c);
@@ -713,7 +756,20 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   const std::vector<double>& tco = (c->elementary == DSO_VTV) ? c->coeffs.b_unq : avals;
   const int na = (int)vco.size(), nb = (int)tco.size();
   const int NP = c->S * (c->S + 1) / 2;
-  CK(cudaMalloc(&c->Utab, (size_t)c->B * na * NP * c->P * c->esz()));
+  // Sec. II F's memory/time trade-off: one potential table per unique
+  // coefficient, or (operators built per action) the coefficient-free part
+  // of U per point and two table slots filled before each potential pass.
+  // DSO_OPERATORS_AUTO builds the tables when they take at most half the
+  // free device memory.
+  const size_t table_bytes = (size_t)c->B * na * NP * c->P * c->esz();
+  bool otf = c->op_mode == DSO_OPERATORS_ON_THE_FLY;
+  if (c->op_mode == DSO_OPERATORS_AUTO && allow_otf) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    otf = table_bytes > free_b / 2;
+  }
+  c->otf = otf;
+  CK(cudaMalloc(&c->Utab, otf ? (size_t)c->B * 2 * NP * c->P * c->esz() : table_bytes));
   const bool sep = kin_axes(c);
   CK(cudaMalloc(&c->tau, (size_t)nb * (sep ? axis_table_len(c) : c->P) * c->esz()));
   CK(cudaMalloc(&c->tau_a, (size_t)na * sizeof(double)));
@@ -723,10 +779,19 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
   for (int u = 0; u < na; ++u) ta[u] = vco[u] * dt;
   CK(cudaMemcpyAsync(c->tau_a, ta.data(), na * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaGetLastError());
-  for (int b = 0; b < c->B; ++b) {
-    CK(launch_potential_tables(at(c->Utab, (size_t)b * na * NP * c->P, c->esz()), c->prec == DSO_FP32,
-                               c->V + (size_t)b * NP * c->P, c->tau_a, na, c->S, c->P, c->stream));
-    c->launches += 1;
+  if (otf) {
+    const size_t nc = (size_t)eig_cache_doubles(c->S);
+    CK(cudaMalloc(&c->eig, (size_t)c->B * nc * c->P * sizeof(double)));
+    for (int b = 0; b < c->B; ++b) {
+      CK(launch_eig_cache(c->eig + (size_t)b * nc * c->P, c->V + (size_t)b * NP * c->P, c->S, c->P, c->stream));
+      c->launches += 1;
+    }
+  } else {
+    for (int b = 0; b < c->B; ++b) {
+      CK(launch_potential_tables(at(c->Utab, (size_t)b * na * NP * c->P, c->esz()), c->prec == DSO_FP32,
+                                 c->V + (size_t)b * NP * c->P, c->tau_a, na, c->S, c->P, c->stream));
+      c->launches += 1;
+    }
   }
   std::vector<double> coef = host_kinetic_coefficients(c->D, c->qmin, c->qmax, c->mass, tco, dt);
   double* dcoef = nullptr;
@@ -756,9 +821,9 @@ dso_status ensure_tables(dso_ctx* c, double dt) {
 // stream of jobs of one shape (a serving loop) tunes once.
 // The key holds everything that fixes the pass kinds and their lines: the
 // grid, S (which with the pass limits fixes the virtual axes), the batch,
-// precision, elementary method, device, the form of the kinetic step and the
-// plane-pass mode.
-using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int, int>;
+// precision, elementary method, device, the form of the kinetic step, the
+// plane-pass mode and whether the potential operators are built per action.
+using TuneKey = std::tuple<int, int64_t, int64_t, int64_t, int, int, int, int, int, int, int, int, int, int>;
 struct TuneVal {
   int G[DSO_MAX_VAXES][2];
   int variant[DSO_MAX_VAXES][2];
@@ -770,7 +835,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 TuneKey tune_key(const dso_ctx* c) {
   return TuneKey(c->D, c->n[0], c->n[1], c->n[2], c->S, c->B, c->prec, c->elementary, c->device, c->max_line,
-                 c->max_tile, kin_axes(c) ? 1 : 0, c->plane_mode);
+                 c->max_tile, kin_axes(c) ? 1 : 0, c->plane_mode, c->otf ? 1 : 0);
 }
 
 dso_status autotune_tiles(dso_ctx* c) {
@@ -2062,6 +2127,23 @@ dso_status dso_set_kinetic_mode(dso_ctx* c, int mode) {
   return DSO_OK;
 }
 
+dso_status dso_set_operator_mode(dso_ctx* c, int mode) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  if (mode != DSO_OPERATORS_AUTO && mode != DSO_OPERATORS_TABLES && mode != DSO_OPERATORS_ON_THE_FLY)
+    return fail(DSO_EINVAL, "mode must be DSO_OPERATORS_AUTO, DSO_OPERATORS_TABLES or DSO_OPERATORS_ON_THE_FLY");
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_tables(c);
+  c->op_mode = mode;
+  c->tuned = false;  // the passes' costs change
+  return DSO_OK;
+}
+
+int dso_operators_on_the_fly(const dso_ctx* c) {
+  if (!c) return fail(DSO_EINVAL, "null context");
+  return c->tables_valid && c->otf ? 1 : 0;
+}
+
 dso_status dso_set_plane_pass(dso_ctx* c, int mode) {
   if (!c) return fail(DSO_EINVAL, "null context");
   if (mode != DSO_PLANE_AUTO && mode != DSO_PLANE_OFF && mode != DSO_PLANE_ON)
@@ -2271,7 +2353,7 @@ dso_status dso_batch_add(dso_batch* b, dso_ctx* c, double t, double dt, int* slo
   BatchSlot s;
   try {
     st = ensure_coeffs(c);
-    if (st == DSO_OK) st = ensure_tables(c, dt);
+    if (st == DSO_OK) st = ensure_tables(c, dt, false);
     if (st != DSO_OK) return st;
     for (int d = 0; d < c->Dv; ++d) {
       c->G[d][0] = batch_G(c, (int)c->nv[d], 1);

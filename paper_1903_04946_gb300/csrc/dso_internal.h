@@ -159,6 +159,16 @@ cudaError_t launch_split_twiddles(void* xtw, bool fp32, int64_t n1, int64_t n2, 
 // FP64 throughout; stored as double2, or rounded once to float2 when fp32.
 cudaError_t launch_potential_tables(void* U, bool fp32, const double* V, const double* tau_a, int na, int S,
                                     long long P, cudaStream_t st);
+// Operators built per action (dso_set_operator_mode): the coefficient-free
+// part of every point's U -- for S = 2 the mean, half difference and
+// coupling of V and the rotation rate, for S >= 3 the eigenvectors and
+// eigenvalues of V -- stored once as [eig_cache_doubles(S)][P] doubles, and
+// U for the one coefficient tau_a[0] assembled from it into U ([NP][P]) with
+// potential_table_kernel's arithmetic (bitwise its table).
+int eig_cache_doubles(int S);
+cudaError_t launch_eig_cache(double* E, const double* V, int S, long long P, cudaStream_t st);
+cudaError_t launch_unitary_from_cache(void* U, bool fp32, const double* E, const double* tau_a, int S, long long P,
+                                      cudaStream_t st);
 
 // Observables (observables.cu): per-block partial sums then a fixed-order
 // final reduction.  `spec` holds |psi~|^2-weighting per axis (p^2 / 2m).

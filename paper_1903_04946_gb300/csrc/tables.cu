@@ -220,33 +220,27 @@ __device__ void jacobi_eig(double (&A)[S][S], double (&W)[S][S], double (&lam)[S
   for (int i = 0; i < S; ++i) lam[i] = A[i][i];
 }
 
-template <int S, typename OutC>
-__global__ void potential_table_kernel(OutC* __restrict__ U, const double* __restrict__ V,
-                                       const double* __restrict__ tau_a, int na, long long P) {
-  constexpr int NP = S * (S + 1) / 2;
-  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (g >= P) return;
+// The per-point part of U_a(q) = exp(-i a dt V(q)) that does not depend on
+// the coefficient: for S = 2 the mean, the half difference and the coupling
+// of the diagonal entries and the rotation rate r; for S >= 3 the
+// eigenvectors W and eigenvalues lam of V(q).  NC doubles per point.
+template <int S>
+struct EigPoint {
+  static constexpr int NC = S == 2 ? 4 : S * S + S;
+  double v0, vz, vx, r;       // S = 2
+  double W[S][S], lam[S];     // S >= 3
+};
+
+template <int S>
+__device__ __forceinline__ void eig_point(const double* __restrict__ V, long long g, long long P, EigPoint<S>& e) {
   if constexpr (S == 2) {
     const double v11 = V[g], v12 = V[P + g], v22 = V[2 * P + g];
-    const double v0 = 0.5 * (v11 + v22), vz = 0.5 * (v11 - v22), vx = v12;
-    const double r = sqrt(vx * vx + vz * vz);
-    for (int u = 0; u < na; ++u) {
-      const double t = tau_a[u];
-      double sr, cr, sg, cg;
-      sincos(r * t, &sr, &cr);
-      const double s_over_r = (r > 0.0) ? sr / r : t;
-      sincos(-t * v0, &sg, &cg);  // exp(-i t v0) = cg + i sg
-      // U = exp(-i t v0) [cos(r t) 1 - i sin(r t)/r (vx sx + vz sz)]
-      const double2 d0 = make_double2(cr, -s_over_r * vz);  // c - i s vz
-      const double2 d1 = make_double2(cr, s_over_r * vz);   // c + i s vz
-      const double2 od = make_double2(0.0, -s_over_r * vx); // -i s vx
-      OutC* out = U + (size_t)u * NP * P;
-      store_c(&out[g], cg * d0.x - sg * d0.y, cg * d0.y + sg * d0.x);
-      store_c(&out[P + g], cg * od.x - sg * od.y, cg * od.y + sg * od.x);
-      store_c(&out[2 * P + g], cg * d1.x - sg * d1.y, cg * d1.y + sg * d1.x);
-    }
+    e.v0 = 0.5 * (v11 + v22);
+    e.vz = 0.5 * (v11 - v22);
+    e.vx = v12;
+    e.r = sqrt(e.vx * e.vx + e.vz * e.vz);
   } else {
-    double A[S][S], W[S][S], lam[S];
+    double A[S][S];
     int k = 0;
     for (int r = 0; r < S; ++r)
       for (int c = r; c < S; ++c) {
@@ -255,26 +249,93 @@ __global__ void potential_table_kernel(OutC* __restrict__ U, const double* __res
         A[c][r] = v;
         ++k;
       }
-    jacobi_eig<S>(A, W, lam);
-    for (int u = 0; u < na; ++u) {
-      const double t = tau_a[u];
-      double ph_re[S], ph_im[S];
-      for (int m = 0; m < S; ++m) sincos(-t * lam[m], &ph_im[m], &ph_re[m]);
-      OutC* out = U + (size_t)u * NP * P;
-      int kk = 0;
-      for (int r = 0; r < S; ++r)
-        for (int c = r; c < S; ++c) {
-          double re = 0.0, im = 0.0;
-          for (int m = 0; m < S; ++m) {
-            const double w = W[r][m] * W[c][m];
-            re += w * ph_re[m];
-            im += w * ph_im[m];
-          }
-          store_c(&out[(size_t)kk * P + g], re, im);
-          ++kk;
-        }
-    }
+    jacobi_eig<S>(A, e.W, e.lam);
   }
+}
+
+// The packed S(S+1)/2 entries of U at point g for coefficient t = a dt.
+template <int S, typename OutC>
+__device__ __forceinline__ void store_unitary(const EigPoint<S>& e, double t, OutC* __restrict__ out, long long g,
+                                              long long P) {
+  if constexpr (S == 2) {
+    double sr, cr, sg, cg;
+    sincos(e.r * t, &sr, &cr);
+    const double s_over_r = (e.r > 0.0) ? sr / e.r : t;
+    sincos(-t * e.v0, &sg, &cg);  // exp(-i t v0) = cg + i sg
+    // U = exp(-i t v0) [cos(r t) 1 - i sin(r t)/r (vx sx + vz sz)]
+    const double2 d0 = make_double2(cr, -s_over_r * e.vz);  // c - i s vz
+    const double2 d1 = make_double2(cr, s_over_r * e.vz);   // c + i s vz
+    const double2 od = make_double2(0.0, -s_over_r * e.vx); // -i s vx
+    store_c(&out[g], cg * d0.x - sg * d0.y, cg * d0.y + sg * d0.x);
+    store_c(&out[P + g], cg * od.x - sg * od.y, cg * od.y + sg * od.x);
+    store_c(&out[2 * P + g], cg * d1.x - sg * d1.y, cg * d1.y + sg * d1.x);
+  } else {
+    double ph_re[S], ph_im[S];
+    for (int m = 0; m < S; ++m) sincos(-t * e.lam[m], &ph_im[m], &ph_re[m]);
+    int kk = 0;
+    for (int r = 0; r < S; ++r)
+      for (int c = r; c < S; ++c) {
+        double re = 0.0, im = 0.0;
+        for (int m = 0; m < S; ++m) {
+          const double w = e.W[r][m] * e.W[c][m];
+          re += w * ph_re[m];
+          im += w * ph_im[m];
+        }
+        store_c(&out[(size_t)kk * P + g], re, im);
+        ++kk;
+      }
+  }
+}
+
+template <int S, typename OutC>
+__global__ void potential_table_kernel(OutC* __restrict__ U, const double* __restrict__ V,
+                                       const double* __restrict__ tau_a, int na, long long P) {
+  constexpr int NP = S * (S + 1) / 2;
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= P) return;
+  EigPoint<S> e;
+  eig_point<S>(V, g, P, e);
+  for (int u = 0; u < na; ++u) store_unitary<S>(e, tau_a[u], U + (size_t)u * NP * P, g, P);
+}
+
+// The coefficient-independent part of every point, stored [NC][P].
+template <int S>
+__global__ void eig_cache_kernel(double* __restrict__ E, const double* __restrict__ V, long long P) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= P) return;
+  EigPoint<S> e;
+  eig_point<S>(V, g, P, e);
+  if constexpr (S == 2) {
+    E[g] = e.v0;
+    E[P + g] = e.vz;
+    E[2 * P + g] = e.vx;
+    E[3 * P + g] = e.r;
+  } else {
+    for (int r = 0; r < S; ++r)
+      for (int c = 0; c < S; ++c) E[(size_t)(r * S + c) * P + g] = e.W[r][c];
+    for (int m = 0; m < S; ++m) E[(size_t)(S * S + m) * P + g] = e.lam[m];
+  }
+}
+
+// U for the one coefficient tau_a[0] from the stored part: the values are
+// reloaded exactly, so the entries are potential_table_kernel's, bit for bit.
+template <int S, typename OutC>
+__global__ void unitary_from_cache_kernel(OutC* __restrict__ U, const double* __restrict__ E,
+                                          const double* __restrict__ tau_a, long long P) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= P) return;
+  EigPoint<S> e;
+  if constexpr (S == 2) {
+    e.v0 = E[g];
+    e.vz = E[P + g];
+    e.vx = E[2 * P + g];
+    e.r = E[3 * P + g];
+  } else {
+    for (int r = 0; r < S; ++r)
+      for (int c = 0; c < S; ++c) e.W[r][c] = E[(size_t)(r * S + c) * P + g];
+    for (int m = 0; m < S; ++m) e.lam[m] = E[(size_t)(S * S + m) * P + g];
+  }
+  store_unitary<S>(e, tau_a[0], U, g, P);
 }
 
 template <typename OutC>
@@ -290,12 +351,44 @@ cudaError_t launch_potential_tables_t(OutC* U, const double* V, const double* ta
   return cudaGetLastError();
 }
 
+template <typename OutC>
+cudaError_t launch_unitary_from_cache_t(OutC* U, const double* E, const double* tau_a, int S, long long P,
+                                        cudaStream_t st) {
+  const unsigned blocks = (unsigned)((P + 127) / 128);
+  switch (S) {
+    case 2: unitary_from_cache_kernel<2><<<blocks, 128, 0, st>>>(U, E, tau_a, P); break;
+    case 3: unitary_from_cache_kernel<3><<<blocks, 128, 0, st>>>(U, E, tau_a, P); break;
+    case 4: unitary_from_cache_kernel<4><<<blocks, 128, 0, st>>>(U, E, tau_a, P); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_potential_tables(void* U, bool fp32, const double* V, const double* tau_a, int na, int S,
                                     long long P, cudaStream_t st) {
   return fp32 ? launch_potential_tables_t((float2*)U, V, tau_a, na, S, P, st)
               : launch_potential_tables_t((double2*)U, V, tau_a, na, S, P, st);
+}
+
+int eig_cache_doubles(int S) { return S == 2 ? 4 : S * S + S; }
+
+cudaError_t launch_eig_cache(double* E, const double* V, int S, long long P, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((P + 127) / 128);
+  switch (S) {
+    case 2: eig_cache_kernel<2><<<blocks, 128, 0, st>>>(E, V, P); break;
+    case 3: eig_cache_kernel<3><<<blocks, 128, 0, st>>>(E, V, P); break;
+    case 4: eig_cache_kernel<4><<<blocks, 128, 0, st>>>(E, V, P); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unitary_from_cache(void* U, bool fp32, const double* E, const double* tau_a, int S, long long P,
+                                      cudaStream_t st) {
+  return fp32 ? launch_unitary_from_cache_t((float2*)U, E, tau_a, S, P, st)
+              : launch_unitary_from_cache_t((double2*)U, E, tau_a, S, P, st);
 }
 
 }  // namespace dso

@@ -148,7 +148,7 @@ def test_library_optimal_coefficients_match_oracle(lib, order):
 
 
 @pytest.mark.parametrize("name,arg", [("dso_set_plane_pass", 1), ("dso_set_kinetic_mode", 1),
-                                      ("dso_set_boundary_merge", 1)])
+                                      ("dso_set_operator_mode", 1), ("dso_set_boundary_merge", 1)])
 def test_mode_setters_reject_a_null_context(lib, name, arg):
     """The mode setters check their context before touching a device."""
     assert getattr(lib, name)(None, arg) == dso.DSO_EINVAL
