@@ -32,6 +32,7 @@ T_FINAL = 2000.0
 SEED = 1904
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PLANE_MODES = {"auto": -1, "off": 0, "on": 1}  # DSO_PLANE_AUTO / _OFF / _ON
+OPERATOR_MODES = {"auto": -1, "tables": 0, "on_the_fly": 1}  # DSO_OPERATORS_AUTO / _TABLES / _ON_THE_FLY
 
 # Workloads.  The default is the 64^3 three-surface FP64 propagation the
 # metric is quoted on; "precision128" is the FP32 storage-and-FFT mode on a
@@ -310,6 +311,7 @@ def run_gpu(args):
     kin_mode = {"auto": dso.DSO_KINETIC_AUTO, "joint": dso.DSO_KINETIC_JOINT, "axes": dso.DSO_KINETIC_AXES}[args.kinetic]
     dso.dso_set_kinetic_mode(ctx.ctx, kin_mode)
     dso.dso_set_plane_pass(ctx.ctx, PLANE_MODES[args.plane])
+    dso.dso_set_operator_mode(ctx.ctx, OPERATOR_MODES[args.operators])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{device}")
 
     def barrier():
@@ -489,6 +491,7 @@ def run_gpu(args):
                                                                        np.sum(np.abs(a64) ** 2))),
                      "norm_drift": float(abs(n32 - 1.0)), "reference": "FP64 GPU path, same input and steps"}
 
+    operators = "built per action" if dso.dso_operators_on_the_fly(ctx.ctx) else "precomputed per unique coefficient"
     ctx.close()
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras and W.get("name", "pyrazine64") == "pyrazine64":
@@ -514,7 +517,7 @@ def run_gpu(args):
                                        "substeps_per_step": nsub, "grid_points": pts,
                                        "kinetic_step": "per axis" if (args.kinetic == "axes" or
                                                                       (args.kinetic == "auto" and fp32))
-                                       else "joint"}),
+                                       else "joint", "potential_operators": operators}),
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clk,
                 "graph_replay": graph}
         if cpu is not None:
@@ -861,6 +864,8 @@ def main():
                     help="skip the sub-records (FP32 precision mode, time to 1e-10, serving)")
     ap.add_argument("--workload", default="pyrazine64", choices=sorted(WORKLOADS))
     ap.add_argument("--order", type=int, default=0, help="override the workload's composition order")
+    ap.add_argument("--operators", default="auto", choices=["auto", "tables", "on_the_fly"],
+                    help="potential operators precomputed or built per action (dso_set_operator_mode)")
     ap.add_argument("--plane", default="auto", choices=["auto", "on", "off"],
                     help="plane pass of the per-axis kinetic step on the two last axes (dso_set_plane_pass)")
     ap.add_argument("--kinetic", default="auto", choices=["auto", "joint", "axes"],
