@@ -867,7 +867,7 @@ def main():
     ap.add_argument("--operators", default="auto", choices=["auto", "tables", "on_the_fly"],
                     help="potential operators precomputed or built per action (dso_set_operator_mode)")
     ap.add_argument("--plane", default="auto", choices=["auto", "on", "off"],
-                    help="plane pass of the per-axis kinetic step on the two last axes (dso_set_plane_pass)")
+                    help="plane pass: the kinetic passes of the two last axes in one launch (dso_set_plane_pass)")
     ap.add_argument("--kinetic", default="auto", choices=["auto", "joint", "axes"],
                     help="form of the kinetic step (dso_set_kinetic_mode); auto: per axis in FP32, joint in FP64")
     ap.add_argument("--profile-steps", type=int, default=0,
