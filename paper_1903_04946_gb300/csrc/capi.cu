@@ -1065,7 +1065,8 @@ dso_status autotune_tiles(dso_ctx* c) {
       std::memcpy(c->cps, cand[k].cps, sizeof(c->cps));
       float ms = 0.f;
       if (!time_mid(mid, ms)) break;
-      if (verbose) fprintf(stderr, "dso autotune: whole-step candidate %d: %.2f us per middle step\n", k, ms * 1000.f / 3.f);
+      if (verbose)
+        fprintf(stderr, "dso autotune: whole-step candidate %d: %.2f us per middle step\n", k, ms * 1000.f / 3.f);
       if (ms < bestStep) {
         bestStep = ms;
         pick = k;
@@ -1111,7 +1112,8 @@ dso_status autotune_tiles(dso_ctx* c) {
       if (plane_active(c)) {
         float ms = 0.f;
         const bool ok = time_mid(step_passes(c, false), ms);
-        if (verbose && ok) fprintf(stderr, "dso autotune: with the plane pass: %.2f us per middle step\n", ms * 1000.f / 3.f);
+        if (verbose && ok)
+          fprintf(stderr, "dso autotune: with the plane pass: %.2f us per middle step\n", ms * 1000.f / 3.f);
         c->plane_on = ok && ms < bestStep;
       } else {
         c->plane_on = false;
